@@ -1,0 +1,284 @@
+/*
+ * Oracle for Hercules exact k-NN query answering (Echihabi et al., "Hercules
+ * Against Data Series Similarity Search", PVLDB 15(10), 2022).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously correct CPU
+ * restatement of what the query path computes.  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark load it.  It shares no
+ * code, header, table or constant generator with the CUDA library.
+ *
+ * Arithmetic: IEEE binary64, round to nearest, no FMA contraction (the file is
+ * compiled with -ffp-contract=off), every sum taken sequentially in index
+ * order.  Functions:
+ *
+ *   hko_dist2        squared Euclidean distance (Sec. 2, k-NN definition and
+ *                    the Euclidean distance it is defined with)
+ *   hko_knn_update   brute-force k-NN: running top-k by (distance, id)
+ *                    (Sec. 2, k-NN query definition; ties broken by lower id)
+ *   hko_seg_stats    mean and population standard deviation of a segment
+ *                    (Sec. 3.2, EAPCA synopsis z_i)
+ *   hko_lb_eapca     LB_EAPCA of a query to a node synopsis (Sec. 2; used by
+ *                    Algorithms Approx-kNN and FindCandidateLeaves, Sec. 3.4;
+ *                    the bound comes from DSTree and is restated below)
+ *   hko_paa          Piecewise Aggregate Approximation (Sec. 2)
+ *   hko_isax_bp      iSAX breakpoints: standard normal quantiles j/256
+ *   hko_isax_symbol  iSAX symbol of a PAA value (alphabet 256, Sec. 2)
+ *   hko_lb_sax       LB_SAX of a query PAA to an iSAX word (Sec. 3.4,
+ *                    Algorithms CSWorker and CRWorker)
+ *
+ * Parity pins for every function live in tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Squared Euclidean distance, summed in index order.                        */
+/* D(q,x) = sum_{j=0}^{n-1} (q_j - x_j)^2, every operation in binary64.      */
+/* ------------------------------------------------------------------------ */
+double hko_dist2(const float *q, const float *x, int n)
+{
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double d = (double)q[j] - (double)x[j];
+        double t = d * d;
+        s = s + t;
+    }
+    return s;
+}
+
+/* (d, id) < (d2, id2) lexicographically. */
+static int pair_less(double d, int64_t id, double d2, int64_t id2)
+{
+    if (d < d2) return 1;
+    if (d > d2) return 0;
+    return id < id2;
+}
+
+/* Insert (d, id) into the ascending list (ds, ids) of length k if it beats
+ * the last entry; the last entry falls off. */
+static void topk_insert(double *ds, int64_t *ids, int k, double d, int64_t id)
+{
+    if (!pair_less(d, id, ds[k - 1], ids[k - 1])) return;
+    int p = k - 1;
+    while (p > 0 && pair_less(d, id, ds[p - 1], ids[p - 1])) {
+        ds[p] = ds[p - 1];
+        ids[p] = ids[p - 1];
+        --p;
+    }
+    ds[p] = d;
+    ids[p] = id;
+}
+
+typedef struct {
+    const float *X;
+    int64_t id0, cnt;
+    int n;
+    const float *Q;
+    int k;
+    int64_t *ids;
+    double *d2;
+    int q_begin, q_end;
+} knn_job;
+
+static void *knn_worker(void *arg)
+{
+    knn_job *J = (knn_job *)arg;
+    for (int qi = J->q_begin; qi < J->q_end; ++qi) {
+        const float *q = J->Q + (int64_t)qi * J->n;
+        double *ds = J->d2 + (int64_t)qi * J->k;
+        int64_t *is = J->ids + (int64_t)qi * J->k;
+        for (int64_t r = 0; r < J->cnt; ++r) {
+            double d = hko_dist2(q, J->X + r * J->n, J->n);
+            topk_insert(ds, is, J->k, d, J->id0 + r);
+        }
+    }
+    return NULL;
+}
+
+/* Initialise nq running top-k lists to (+inf, -1). */
+void hko_knn_init(int nq, int k, int64_t *ids, double *d2)
+{
+    for (int64_t i = 0; i < (int64_t)nq * k; ++i) {
+        ids[i] = -1;
+        d2[i] = INFINITY;
+    }
+}
+
+/* Brute-force k-NN, one block of consecutive series at a time.
+ * X: cnt rows of n floats whose ids are id0, id0+1, ...; Q: nq rows of n
+ * floats; ids/d2: nq*k running lists (ascending by (D, id)).  Calling this
+ * over consecutive blocks of a collection gives the same lists as one call
+ * over the whole collection: every series is offered to every query's list,
+ * in id order.  Queries are divided among nthreads threads. */
+int hko_knn_update(const float *X, int64_t id0, int64_t cnt, int n,
+                   const float *Q, int nq, int k, int64_t *ids, double *d2,
+                   int nthreads)
+{
+    if (n <= 0 || nq < 0 || k <= 0 || cnt < 0) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nq) nthreads = nq > 0 ? nq : 1;
+    knn_job *jobs = (knn_job *)calloc((size_t)nthreads, sizeof(knn_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -2; }
+    for (int t = 0; t < nthreads; ++t) {
+        knn_job *J = &jobs[t];
+        J->X = X; J->id0 = id0; J->cnt = cnt; J->n = n; J->Q = Q; J->k = k;
+        J->ids = ids; J->d2 = d2;
+        J->q_begin = (int)((int64_t)nq * t / nthreads);
+        J->q_end = (int)((int64_t)nq * (t + 1) / nthreads);
+    }
+    int started = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, knn_worker, &jobs[t]) != 0) break;
+        started = t;
+    }
+    knn_worker(&jobs[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    /* any job whose thread failed to start runs here */
+    for (int t = started + 1; t < nthreads; ++t) knn_worker(&jobs[t]);
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* EAPCA segment statistics (Sec. 3.2): mean and population standard         */
+/* deviation of x[a..b).  Two passes: the mean, then the mean square          */
+/* deviation from it.                                                         */
+/* ------------------------------------------------------------------------ */
+void hko_seg_stats(const float *x, int a, int b, double *mu, double *sd)
+{
+    double l = (double)(b - a);
+    double s = 0.0;
+    for (int j = a; j < b; ++j) s = s + (double)x[j];
+    double m = s / l;
+    double v = 0.0;
+    for (int j = a; j < b; ++j) {
+        double d = (double)x[j] - m;
+        double t = d * d;
+        v = v + t;
+    }
+    *mu = m;
+    *sd = sqrt(v / l);
+}
+
+/* Segment statistics of many rows at once: rows[i] of X (row length n). */
+void hko_seg_stats_rows(const float *X, const int64_t *rows, int64_t cnt, int n,
+                        int a, int b, double *mu, double *sd)
+{
+    for (int64_t i = 0; i < cnt; ++i)
+        hko_seg_stats(X + rows[i] * (int64_t)n, a, b, &mu[i], &sd[i]);
+}
+
+/* Distance from v to the closed interval [lo, hi] (0 inside). */
+static double dist_to_range(double v, double lo, double hi)
+{
+    if (v < lo) return lo - v;
+    if (v > hi) return v - hi;
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* LB_EAPCA (Sec. 2; Algorithms Approx-kNN and FindCandidateLeaves prune    */
+/* with it, Sec. 3.4).  The paper takes the bound from DSTree unrestated.     */
+/* For a node with segmentation r_1 < ... < r_m = n (r_0 = 0) and synopsis    */
+/* z_i = {mu_min, mu_max, sd_min, sd_max} (Sec. 3.2), with                    */
+/* l_i = r_i - r_{i-1} and the query's own segment mean and standard          */
+/* deviation (mu_q,i, sd_q,i):                                                */
+/*   LB^2 = sum_i l_i * ( dist(mu_q,i, [mu_min,mu_max])^2                     */
+/*                      + dist(sd_q,i, [sd_min,sd_max])^2 )                   */
+/* It lower-bounds D because, per segment, sum (q-x)^2 =                      */
+/* l (mu_q - mu_x)^2 + |q~ - x~|^2 >= l (mu_q - mu_x)^2 + (|q~| - |x~|)^2     */
+/* = l [(mu_q - mu_x)^2 + (sd_q - sd_x)^2]  (q~, x~ centred, |q~| = sqrt(l) sd) */
+/* seg_end: m right endpoints; env: m*4 doubles (mu_min, mu_max, sd_min,      */
+/* sd_max).  Returns the squared bound.                                       */
+/* ------------------------------------------------------------------------ */
+double hko_lb_eapca(const float *q, int m, const int32_t *seg_end,
+                    const double *env)
+{
+    double lb = 0.0;
+    int a = 0;
+    for (int i = 0; i < m; ++i) {
+        int b = seg_end[i];
+        double mu, sd;
+        hko_seg_stats(q, a, b, &mu, &sd);
+        double dm = dist_to_range(mu, env[4 * i + 0], env[4 * i + 1]);
+        double ds = dist_to_range(sd, env[4 * i + 2], env[4 * i + 3]);
+        double l = (double)(b - a);
+        double t = dm * dm + ds * ds;
+        lb = lb + l * t;
+        a = b;
+    }
+    return lb;
+}
+
+/* ------------------------------------------------------------------------ */
+/* PAA (Sec. 2): w equal segments of length n/w, each the mean of its points.  */
+/* ------------------------------------------------------------------------ */
+void hko_paa(const float *x, int n, int w, double *out)
+{
+    int l = n / w;
+    for (int i = 0; i < w; ++i) {
+        double s = 0.0;
+        for (int j = i * l; j < (i + 1) * l; ++j) s = s + (double)x[j];
+        out[i] = s / (double)l;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* iSAX breakpoints for an alphabet of 256 (Sec. 2): beta_j with              */
+/* Phi(beta_j) = j/256, j = 1..255, Phi the standard normal CDF,              */
+/* Phi(b) = erfc(-b/sqrt(2))/2.  Found by bisection on [-40, 40] until the     */
+/* bracket stops shrinking.                                                   */
+/* ------------------------------------------------------------------------ */
+static double std_normal_cdf(double b) { return 0.5 * erfc(-b / sqrt(2.0)); }
+
+void hko_isax_bp(double *out /* 255 */)
+{
+    for (int j = 1; j <= 255; ++j) {
+        double target = (double)j / 256.0;
+        double lo = -40.0, hi = 40.0;
+        for (int it = 0; it < 400; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid == lo || mid == hi) break;
+            if (std_normal_cdf(mid) < target) lo = mid; else hi = mid;
+        }
+        /* pick the end of the bracket whose CDF is closer to the target */
+        double elo = fabs(std_normal_cdf(lo) - target);
+        double ehi = fabs(std_normal_cdf(hi) - target);
+        out[j - 1] = (elo <= ehi) ? lo : hi;
+    }
+}
+
+/* iSAX symbol of a PAA value: the number of breakpoints (given as float32,
+ * promoted) that are <= v.  A value equal to a breakpoint takes the upper
+ * cell.  Symbols run 0..255; cell s spans [beta_s, beta_{s+1}) with
+ * beta_0 = -inf and beta_256 = +inf. */
+int hko_isax_symbol(double v, const float *bp /* 255 */)
+{
+    int s = 0;
+    for (int j = 0; j < 255; ++j)
+        if ((double)bp[j] <= v) s = s + 1;
+    return s;
+}
+
+/* LB_SAX (Sec. 3.4, Algorithm CSWorker): for a query PAA p (w segments) and an iSAX word
+ * sym (w symbols) of a series of length n:
+ *   LB^2 = (n/w) * sum_i dist(p_i, [beta_{s_i}, beta_{s_i+1}])^2
+ * with beta_0 = -inf, beta_256 = +inf. */
+double hko_lb_sax(const double *paa_q, const uint8_t *sym, int w, int n,
+                  const float *bp /* 255 */)
+{
+    double acc = 0.0;
+    for (int i = 0; i < w; ++i) {
+        int s = sym[i];
+        double lo = (s == 0) ? -INFINITY : (double)bp[s - 1];
+        double hi = (s == 255) ? INFINITY : (double)bp[s];
+        double d = dist_to_range(paa_q[i], lo, hi);
+        acc = acc + d * d;
+    }
+    return ((double)n / (double)w) * acc;
+}
