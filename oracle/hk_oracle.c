@@ -231,16 +231,19 @@ void hko_paa(const float *x, int n, int w, double *out)
 /* ------------------------------------------------------------------------ */
 /* iSAX breakpoints for an alphabet of 256 (Sec. 2): beta_j with              */
 /* Phi(beta_j) = j/256, j = 1..255, Phi the standard normal CDF,              */
-/* Phi(b) = erfc(-b/sqrt(2))/2.  Found by bisection on [-40, 40] until the     */
-/* bracket stops shrinking.                                                   */
+/* Phi(b) = erfc(-b/sqrt(2))/2.  The lower half (j < 128, beta_j < 0) is      */
+/* found by bisection on [-40, 0] until the bracket stops shrinking; the      */
+/* normal's symmetry Phi(-x) = 1 - Phi(x) gives beta_128 = 0 and              */
+/* beta_{256-j} = -beta_j (near 0, Phi is flat to binary64 precision, so      */
+/* bisection alone cannot resolve beta_128).                                   */
 /* ------------------------------------------------------------------------ */
 static double std_normal_cdf(double b) { return 0.5 * erfc(-b / sqrt(2.0)); }
 
 void hko_isax_bp(double *out /* 255 */)
 {
-    for (int j = 1; j <= 255; ++j) {
+    for (int j = 1; j < 128; ++j) {
         double target = (double)j / 256.0;
-        double lo = -40.0, hi = 40.0;
+        double lo = -40.0, hi = 0.0;
         for (int it = 0; it < 400; ++it) {
             double mid = 0.5 * (lo + hi);
             if (mid == lo || mid == hi) break;
@@ -251,6 +254,8 @@ void hko_isax_bp(double *out /* 255 */)
         double ehi = fabs(std_normal_cdf(hi) - target);
         out[j - 1] = (elo <= ehi) ? lo : hi;
     }
+    out[127] = 0.0;
+    for (int j = 129; j <= 255; ++j) out[j - 1] = -out[256 - j - 1];
 }
 
 /* iSAX symbol of a PAA value: the number of breakpoints (given as float32,

@@ -133,8 +133,8 @@ def test_breakpoints_match_scipy_and_symmetry(oracle_lib):
     bp = oracle.isax_breakpoints()
     ref = stats.norm.ppf(np.arange(1, 256) / 256.0)
     np.testing.assert_allclose(bp, ref, rtol=0, atol=1e-13)
-    assert abs(bp[127]) < 1e-15                     # beta_128 = 0
-    np.testing.assert_allclose(bp, -bp[::-1], atol=1e-14)   # beta_{256-j} = -beta_j
+    assert bp[127] == 0.0                            # beta_128 = 0
+    np.testing.assert_array_equal(bp, -bp[::-1])     # beta_{256-j} = -beta_j
     assert np.all(np.diff(bp) > 0)
     # Phi(beta_j) = j/256 with the library's erfc
     for j in (1, 2, 64, 128, 200, 255):
