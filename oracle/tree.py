@@ -19,7 +19,8 @@ one of its segments SG_i = [r_{i-1}, r_i):
 
 Readings where the paper is silent (it defers getBestSplitPolicy to DSTree):
   * root segmentation: 4 equal segments (n divisible by 4);
-  * a V-split cuts [a, b) at floor((a+b)/2), only when b - a >= 2;
+  * a V-split cuts [a, b) at floor((a+b)/2), only when b - a >= 2 and the
+    node has fewer than MAX_SEGMENTS (64) segments;
   * candidates, enumerated in this order (earlier wins a tie): for each segment
     i ascending, for the mean then the std: the H-split on SG_i, the V-split
     on the left half, the V-split on the right half;
@@ -46,6 +47,7 @@ import numpy as np
 from . import seg_stats, seg_stats_rows
 
 ROOT_SEGMENTS = 4
+MAX_SEGMENTS = 64
 
 
 def root_segmentation(n: int):
@@ -89,11 +91,12 @@ def candidates(seg_end):
     """(kind, seg, half, stat, a, b) in tie-break order."""
     out = []
     a = 0
+    can_v = len(seg_end) < MAX_SEGMENTS
     for i, b in enumerate(seg_end):
         mid = (a + b) // 2
         for stat in (0, 1):
             out.append(("H", i, -1, stat, a, b))
-            if b - a >= 2:
+            if b - a >= 2 and can_v:
                 out.append(("V", i, 0, stat, a, mid))
                 out.append(("V", i, 1, stat, mid, b))
         a = b
