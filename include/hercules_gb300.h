@@ -1,0 +1,195 @@
+/*
+ * hercules_gb300.h -- C ABI of the GB300 Hercules exact k-NN library.
+ *
+ * The library builds a Hercules index (Echihabi et al., PVLDB 15(10), 2022)
+ * over N float32 data series of length n, resident in the memory of one GPU,
+ * and answers exact k-NN queries under the Euclidean distance against it.
+ *
+ * Conventions for every entry point:
+ *   - Return value: HK_OK (0) or a negative HK_E* code.  hk_last_error()
+ *     then returns a message for the calling thread.  A failed call leaves
+ *     its outputs unspecified and releases what it allocated.
+ *   - Pointers to series, queries and outputs may be host or device
+ *     memory of the current CUDA device; the library finds out which with
+ *     cudaPointerGetAttributes and copies as needed.  The caller keeps
+ *     ownership of every buffer it passes, except as HK_BUILD_ADOPT says.
+ *   - Layouts are row-major: X[i*n + j] is point j of series i.
+ *   - stream: a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     synchronous with respect to the host: outputs are complete on return.
+ *   - The library never normalises the series (the paper's collections are
+ *     z-normalised beforehand, Sec. 4.1); NaN or Inf in X or Q is rejected.
+ */
+#ifndef HERCULES_GB300_H
+#define HERCULES_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HK_OK 0
+#define HK_EINVAL (-1)    /* bad argument: sizes, null pointers, NaN/Inf     */
+#define HK_ENOMEM (-2)    /* device or host allocation failed                */
+#define HK_ECUDA (-3)     /* a CUDA runtime call failed                      */
+#define HK_ETIMEOUT (-4)  /* a bounded device or host wait ran out           */
+#define HK_EBUSY (-5)     /* the object is in use (server slots full)        */
+#define HK_EINTERNAL (-6) /* an internal consistency check failed            */
+
+#define HK_ISAX_SEGMENTS 16   /* iSAX word length (Sec. 2)                     */
+#define HK_ISAX_ALPHABET 256  /* iSAX alphabet (Sec. 2)                        */
+#define HK_MIN_LEN 16
+#define HK_MAX_LEN 4096
+#define HK_MAX_K 1024
+
+typedef struct hk_index hk_index;
+
+/* Build flags. */
+#define HK_BUILD_ADOPT 1u  /* X is a device buffer from cudaMalloc that the
+                              index takes over and frees once it no longer
+                              needs it (saves one copy of the collection).  */
+#define HK_BUILD_BF16 2u   /* also keep a bfloat16 copy of the collection
+                              and binary64 squared norms (precision form).  */
+
+typedef struct {
+    int32_t leaf_capacity;  /* tau, the leaf threshold (Sec. 3.2); >= 1      */
+    int32_t eval_cap;       /* series a split policy is chosen from: the
+                               node's first min(tau+1, eval_cap); 0 = 4096    */
+    uint32_t flags;         /* HK_BUILD_*                                     */
+    int32_t reserved;
+} hk_build_opts;
+
+/*
+ * hk_build -- build an index (Sec. 3.2-3.3, Algorithm InsertSeriesToNode;
+ * Algorithms WriteIndexWorker / WriteLeafData for the leaf-ordered layout).
+ *
+ * X: N*n float32 (host or device).  N >= 1, 16 <= n <= 4096, n % 16 == 0.
+ * The tree is the one sequential insertion in id order produces with the
+ * library's split policy (4 root segments; H- and V-splits chosen by the
+ * smallest size-weighted synopsis spread).  The raw series are stored in
+ * leaf (inorder) order with their iSAX words (LRDFile/LSDFile, Sec. 3.3).
+ * On success *out owns all device memory of the index; free it with hk_free.
+ */
+int hk_build(const float *X, int64_t N, int32_t n, const hk_build_opts *opts,
+             void *stream, hk_index **out);
+
+int hk_free(hk_index *idx);
+
+typedef struct {
+    int64_t N;
+    int32_t n;
+    int32_t leaf_capacity;
+    int64_t leaves;
+    int32_t max_segments;    /* most segments of any leaf                     */
+    int32_t depth;           /* levels of splits                              */
+    int64_t distinct_segments;
+    int64_t device_bytes;    /* device memory the index holds                 */
+    int32_t has_bf16;
+    int32_t reserved;
+} hk_index_info;
+
+int hk_index_info_get(const hk_index *idx, hk_index_info *out);
+
+/* Query flags. */
+#define HK_Q_NOSAX 1u      /* skip LB_SAX filtering (ablation, Sec. 4.2)      */
+#define HK_Q_NOTHRESH 2u   /* ignore EAPCA_TH / SAX_TH (ablation)             */
+#define HK_Q_NOPRUNE 4u    /* scan every series (parallel-scan baseline)      */
+
+typedef struct {
+    int32_t l_max;        /* leaves visited by the approximate search per query
+                             (Sec. 3.4, Approx-kNN); 0 = 1                     */
+    float eapca_th;       /* EAPCA_TH; < 0 = 0.25 (Sec. 4.2)                   */
+    float sax_th;         /* SAX_TH; < 0 = 0.50 (Sec. 4.2)                     */
+    uint32_t flags;       /* HK_Q_*                                            */
+    int32_t query_group;  /* queries sharing one scan work item; 0 = auto      */
+    int32_t series_tile;  /* series per scan work item; 0 = auto              */
+} hk_query_opts;
+
+typedef struct {
+    int64_t queries;
+    int64_t leaves_total;         /* leaves x queries                          */
+    int64_t leaves_approx;        /* (leaf, query) pairs of the approximate step */
+    int64_t leaves_candidate;     /* (leaf, query) pairs in LCList               */
+    int64_t series_candidate;     /* (series, query) pairs in candidate leaves   */
+    int64_t series_sax_pruned;    /* pruned by LB_SAX                            */
+    int64_t series_abandoned;     /* distance computation abandoned early        */
+    int64_t series_full;          /* distance computed over all n points         */
+    int64_t points_computed;      /* (q - x)^2 terms evaluated                   */
+    int64_t rescored;             /* binary64 boundary rescores                  */
+    int64_t fallback_queries;     /* queries finished by the exhaustive collect  */
+    int64_t work_items;           /* scan work items launched                    */
+    int64_t skip_sequential;      /* queries scanned without LB_SAX (EAPCA_TH)   */
+    int64_t reserved[3];
+} hk_query_stats;
+
+/*
+ * hk_query -- exact k-NN (Sec. 3.4, Algorithm Exact-kNN and its steps
+ * Approx-kNN, FindCandidateLeaves, CSWorker, CRWorker), for nq queries
+ * answered together.
+ *
+ * Q: nq*n float32 (host or device).  1 <= k <= min(N, 1024).
+ * out_ids: nq*k int64 original row ids; out_dist: nq*k float32 Euclidean
+ * distances (sqrt of the binary64 squared distance, rounded to float32).
+ * Row i lists query i's neighbours ascending by (binary64 squared distance
+ * summed in index order, id): the brute-force answer, ties to the lower id.
+ * stats may be NULL; opts may be NULL (defaults).
+ */
+int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k,
+             const hk_query_opts *opts, void *stream, int64_t *out_ids,
+             float *out_dist, hk_query_stats *stats);
+
+/*
+ * hk_scan_knn -- exact k-NN by scanning every series of a collection (no
+ * index): the parallel scan the paper compares against (PSCAN, Sec. 2 and
+ * Sec. 4.1), with the same answer definition and outputs as hk_query.
+ * X: N*n float32, Q: nq*n float32 (host or device).
+ */
+int hk_scan_knn(const float *X, int64_t N, int32_t n, const float *Q,
+                int32_t nq, int32_t k, void *stream, int64_t *out_ids,
+                float *out_dist);
+
+/*
+ * hk_isax_breakpoints -- the 255 iSAX breakpoints the library uses
+ * (Sec. 2: alphabet 256; beta_j the standard normal quantile of j/256),
+ * as float32.  Host-only; needs no GPU.
+ */
+int hk_isax_breakpoints(float out[255]);
+
+/* ---- inspection: copies of index internals and single steps, for tests ---- */
+
+/*
+ * hk_index_export -- copy the leaf layout to host buffers (any may be NULL):
+ *   perm[N]            original id of the series at each leaf-order position
+ *   leaf_off[L+1]      first position of each leaf (inorder)
+ *   leaf_nseg[L]       segments of each leaf
+ *   seg_end[L*64]      right endpoints of each leaf's segments (row of 64)
+ *   env[L*64*4]        synopsis (mu_min, mu_max, sd_min, sd_max) per segment,
+ *                      binary64 (Sec. 3.2)
+ *   sax[N*16]          iSAX words in leaf order
+ * L = hk_index_info.leaves; max_segments <= 64.
+ */
+int hk_index_export(const hk_index *idx, int64_t *perm, int64_t *leaf_off,
+                    int32_t *leaf_nseg, int32_t *seg_end, double *env,
+                    uint8_t *sax);
+
+/*
+ * hk_debug_lb_eapca -- LB_EAPCA (squared, binary64) of each query to each
+ * leaf synopsis: out[q*L + leaf].  Q host or device; out host.
+ */
+int hk_debug_lb_eapca(hk_index *idx, const float *Q, int32_t nq, double *out);
+
+/*
+ * hk_debug_lb_sax -- the certified lower value of LB_SAX (squared, float32)
+ * that the scan compares, for each query and each series in leaf order:
+ * out[q*N + pos].  Q host or device; out host.
+ */
+int hk_debug_lb_sax(hk_index *idx, const float *Q, int32_t nq, float *out);
+
+const char *hk_last_error(void);
+const char *hk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HERCULES_GB300_H */

@@ -1,0 +1,237 @@
+"""ctypes binding of the C ABI in include/hercules_gb300.h.
+
+Argument marshalling only: every step of index building and query answering
+runs in the CUDA library.  There is no CPU fallback; if the library has not
+been built, loading it raises.
+
+Raw entry points keep their C names (hk_build, hk_query, ...).  `Index` and
+`scan_knn` wrap them for torch tensors and numpy arrays.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhercules_gb300.so")
+
+HK_OK = 0
+HK_EINVAL = -1
+HK_ENOMEM = -2
+HK_ECUDA = -3
+HK_ETIMEOUT = -4
+HK_EBUSY = -5
+HK_EINTERNAL = -6
+
+HK_BUILD_ADOPT = 1
+HK_BUILD_BF16 = 2
+HK_Q_NOSAX = 1
+HK_Q_NOTHRESH = 2
+HK_Q_NOPRUNE = 4
+
+
+class hk_build_opts(ctypes.Structure):
+    _fields_ = [("leaf_capacity", ctypes.c_int32), ("eval_cap", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+class hk_query_opts(ctypes.Structure):
+    _fields_ = [("l_max", ctypes.c_int32), ("eapca_th", ctypes.c_float),
+                ("sax_th", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("query_group", ctypes.c_int32), ("series_tile", ctypes.c_int32)]
+
+
+class hk_query_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "queries", "leaves_total", "leaves_approx", "leaves_candidate", "series_candidate",
+        "series_sax_pruned", "series_abandoned", "series_full", "points_computed", "rescored",
+        "fallback_queries", "work_items", "skip_sequential", "r0", "r1", "r2")]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if not f[0].startswith("r") or
+                f[0] == "rescored"}
+
+
+class hk_index_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("n", ctypes.c_int32), ("leaf_capacity", ctypes.c_int32),
+                ("leaves", ctypes.c_int64), ("max_segments", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("distinct_segments", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("has_bf16", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class HerculesError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hercules error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+# every symbol include/hercules_gb300.h declares
+EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_scan_knn",
+           "hk_isax_breakpoints", "hk_index_export", "hk_debug_lb_eapca", "hk_debug_lb_sax",
+           "hk_last_error", "hk_version"]
+
+
+def lib():
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library not built: %s missing (run "
+                               "__graft_entry__.build())" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L.hk_build.argtypes = [vp, ctypes.c_int64, ctypes.c_int32,
+                               ctypes.POINTER(hk_build_opts), vp, ctypes.POINTER(vp)]
+        L.hk_free.argtypes = [vp]
+        L.hk_index_info_get.argtypes = [vp, ctypes.POINTER(hk_index_info)]
+        L.hk_query.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.POINTER(hk_query_opts), vp, vp, vp,
+                               ctypes.POINTER(hk_query_stats)]
+        L.hk_scan_knn.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, ctypes.c_int32,
+                                  ctypes.c_int32, vp, vp, vp]
+        L.hk_isax_breakpoints.argtypes = [vp]
+        L.hk_index_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.hk_debug_lb_eapca.argtypes = [vp, vp, ctypes.c_int32, vp]
+        L.hk_debug_lb_sax.argtypes = [vp, vp, ctypes.c_int32, vp]
+        L.hk_last_error.restype = ctypes.c_char_p
+        L.hk_version.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("hk_last_error", "hk_version"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != HK_OK:
+        raise HerculesError(rc, lib().hk_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a torch tensor or numpy array (contiguous)."""
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def isax_breakpoints():
+    out = np.empty(255, np.float32)
+    _check(lib().hk_isax_breakpoints(_ptr(out)))
+    return out
+
+
+def _is_cuda(t):
+    return hasattr(t, "is_cuda") and t.is_cuda
+
+
+def _out_like(like, shape, np_dtype, torch_dtype):
+    if _is_cuda(like):
+        import torch
+        return torch.empty(shape, dtype=torch_dtype, device=like.device)
+    return np.empty(shape, np_dtype)
+
+
+class Index:
+    """A Hercules index resident on the current GPU (owns its device memory)."""
+
+    def __init__(self, X, leaf_capacity: int, eval_cap: int = 0, flags: int = 0, stream=None):
+        N, n = X.shape
+        o = hk_build_opts(int(leaf_capacity), int(eval_cap), int(flags), 0)
+        h = ctypes.c_void_p()
+        _check(lib().hk_build(_ptr(X), N, n, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.N, self.n = N, n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hk_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        i = hk_index_info()
+        _check(lib().hk_index_info_get(self._h, ctypes.byref(i)))
+        return {f[0]: getattr(i, f[0]) for f in i._fields_ if f[0] != "reserved"}
+
+    def query(self, Q, k: int, l_max=0, eapca_th=-1.0, sax_th=-1.0, flags=0, query_group=0,
+              series_tile=0, stream=None, out=None):
+        """(ids [nq,k] int64, dist [nq,k] float32, stats dict).  Outputs live
+        where Q lives (device tensors for a CUDA Q, numpy otherwise) unless
+        out=(ids, dist) is given."""
+        nq = Q.shape[0]
+        assert Q.shape[1] == self.n
+        if out is None:
+            ids = _out_like(Q, (nq, k), np.int64, _torch_dtype("int64"))
+            dist = _out_like(Q, (nq, k), np.float32, _torch_dtype("float32"))
+        else:
+            ids, dist = out
+        o = hk_query_opts(int(l_max), float(eapca_th), float(sax_th), int(flags),
+                          int(query_group), int(series_tile))
+        st = hk_query_stats()
+        _check(lib().hk_query(self._h, _ptr(Q), nq, int(k), ctypes.byref(o), _stream(stream),
+                              _ptr(ids), _ptr(dist), ctypes.byref(st)))
+        return ids, dist, st.as_dict()
+
+    def export(self):
+        """Leaf layout as numpy arrays (see hk_index_export)."""
+        info = self.info()
+        L = info["leaves"]
+        perm = np.empty(self.N, np.int64)
+        leaf_off = np.empty(L + 1, np.int64)
+        nseg = np.empty(L, np.int32)
+        seg_end = np.empty((L, 64), np.int32)
+        env = np.empty((L, 64, 4), np.float64)
+        sax = np.empty((self.N, 16), np.uint8)
+        _check(lib().hk_index_export(self._h, _ptr(perm), _ptr(leaf_off), _ptr(nseg),
+                                     _ptr(seg_end), _ptr(env), _ptr(sax)))
+        return dict(perm=perm, leaf_off=leaf_off, nseg=nseg, seg_end=seg_end, env=env, sax=sax)
+
+    def debug_lb_eapca(self, Q):
+        L = self.info()["leaves"]
+        out = np.empty((Q.shape[0], L), np.float64)
+        _check(lib().hk_debug_lb_eapca(self._h, _ptr(Q), Q.shape[0], _ptr(out)))
+        return out
+
+    def debug_lb_sax(self, Q):
+        out = np.empty((Q.shape[0], self.N), np.float32)
+        _check(lib().hk_debug_lb_sax(self._h, _ptr(Q), Q.shape[0], _ptr(out)))
+        return out
+
+
+def _torch_dtype(name):
+    import torch
+    return getattr(torch, name)
+
+
+def scan_knn(X, Q, k: int, stream=None):
+    """Exhaustive exact k-NN (the parallel-scan baseline), no index."""
+    N, n = X.shape
+    nq = Q.shape[0]
+    ids = _out_like(Q, (nq, k), np.int64, _torch_dtype("int64"))
+    dist = _out_like(Q, (nq, k), np.float32, _torch_dtype("float32"))
+    _check(lib().hk_scan_knn(_ptr(X), N, n, _ptr(Q), nq, int(k), _stream(stream), _ptr(ids),
+                             _ptr(dist)))
+    return ids, dist

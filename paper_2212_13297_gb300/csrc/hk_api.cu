@@ -1,0 +1,199 @@
+// C ABI entry points: argument checks, host/device pointer handling, errors.
+#include <cstring>
+#include <memory>
+
+#include "hk_internal.cuh"
+
+namespace hk {
+const char *last_error_cstr();
+}
+
+namespace {
+
+template <class F>
+int guard(F &&f) {
+    try {
+        hk::clear_last_error();
+        f();
+        return HK_OK;
+    } catch (const hk::Error &e) {
+        hk::set_last_error(e.code, e.msg);
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        hk::set_last_error(HK_ENOMEM, "host allocation failed");
+        return HK_ENOMEM;
+    } catch (...) {
+        hk::set_last_error(HK_EINTERNAL, "unexpected exception");
+        return HK_EINTERNAL;
+    }
+}
+
+void check_len(int32_t n) {
+    if (n < HK_MIN_LEN || n > HK_MAX_LEN || n % HK_ISAX_SEGMENTS != 0)
+        hk::fail(HK_EINVAL, "series length n=%d must be in [%d, %d] and divisible by %d", n,
+                 HK_MIN_LEN, HK_MAX_LEN, HK_ISAX_SEGMENTS);
+}
+
+// A device copy of a host array, or the device pointer itself.
+const float *device_view(const float *p, size_t count, cudaStream_t s, hk::DevBuf<float> &tmp) {
+    if (hk::is_device_ptr(p)) return p;
+    tmp.alloc(count, s);
+    HK_CHECK_CUDA(cudaMemcpyAsync(tmp.p, p, count * sizeof(float), cudaMemcpyHostToDevice, s));
+    return tmp.p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hk_version(void) { return "hercules-gb300 0.1 (sm_103a)"; }
+
+const char *hk_last_error(void) { return hk::last_error_cstr(); }
+
+int hk_isax_breakpoints(float out[255]) {
+    return guard([&] {
+        if (!out) hk::fail(HK_EINVAL, "out is NULL");
+        hk::isax_breakpoints(out);
+    });
+}
+
+int hk_build(const float *X, int64_t N, int32_t n, const hk_build_opts *opts, void *stream,
+             hk_index **out) {
+    return guard([&] {
+        if (!out) hk::fail(HK_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (!X) hk::fail(HK_EINVAL, "X is NULL");
+        if (N < 1 || N > 0x7fffffffLL) hk::fail(HK_EINVAL, "N=%lld must be in [1, 2^31-1]", (long long)N);
+        check_len(n);
+        hk_build_opts o;
+        if (opts) {
+            o = *opts;
+        } else {
+            std::memset(&o, 0, sizeof(o));
+            o.leaf_capacity = 1000;
+        }
+        if (o.leaf_capacity < 1) hk::fail(HK_EINVAL, "leaf_capacity=%d must be >= 1", o.leaf_capacity);
+        if (o.eval_cap < 0) hk::fail(HK_EINVAL, "eval_cap=%d must be >= 0", o.eval_cap);
+        cudaStream_t s = (cudaStream_t)stream;
+        const bool dev = hk::is_device_ptr(X);
+        if ((o.flags & HK_BUILD_ADOPT) && !dev) hk::fail(HK_EINVAL, "HK_BUILD_ADOPT needs a device X");
+        std::unique_ptr<hk_index> idx(new hk_index());
+        idx->stream = s;
+        hk::DevBuf<float> tmp;
+        const float *Xd = device_view(X, (size_t)N * n, s, tmp);
+        hk::check_finite(Xd, (int64_t)N * n, s, "X");
+        hk::build_index(idx.get(), Xd, N, n, o, s);
+        tmp.release();
+        if (o.flags & HK_BUILD_ADOPT) HK_CHECK_CUDA(cudaFree(const_cast<float *>(X)));
+        *out = idx.release();
+    });
+}
+
+int hk_free(hk_index *idx) {
+    return guard([&] {
+        if (!idx) return;
+        cudaDeviceSynchronize();
+        delete idx;
+    });
+}
+
+int hk_index_info_get(const hk_index *idx, hk_index_info *out) {
+    return guard([&] {
+        if (!idx || !out) hk::fail(HK_EINVAL, "NULL argument");
+        std::memset(out, 0, sizeof(*out));
+        out->N = idx->N;
+        out->n = idx->n;
+        out->leaf_capacity = idx->tau;
+        out->leaves = idx->L;
+        out->max_segments = idx->max_m;
+        out->depth = idx->depth;
+        out->distinct_segments = idx->S;
+        out->device_bytes = (int64_t)(idx->X.bytes() + idx->perm.bytes() + idx->sax.bytes() +
+                                      idx->leaf_off.bytes() + idx->leaf_nseg.bytes() +
+                                      idx->leaf_seg.bytes() + idx->env.bytes() +
+                                      idx->seg_ab.bytes() + idx->bp.bytes());
+        out->has_bf16 = 0;
+    });
+}
+
+int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k, const hk_query_opts *opts,
+             void *stream, int64_t *out_ids, float *out_dist, hk_query_stats *stats) {
+    return guard([&] {
+        if (!idx || !Q || !out_ids || !out_dist) hk::fail(HK_EINVAL, "NULL argument");
+        if (nq < 1) hk::fail(HK_EINVAL, "nq=%d must be >= 1", nq);
+        if (k < 1 || k > HK_MAX_K || (int64_t)k > idx->N)
+            hk::fail(HK_EINVAL, "k=%d must be in [1, min(N=%lld, %d)]", k, (long long)idx->N, HK_MAX_K);
+        hk_query_opts o;
+        if (opts) {
+            o = *opts;
+        } else {
+            std::memset(&o, 0, sizeof(o));
+            o.eapca_th = -1.0f;
+            o.sax_th = -1.0f;
+        }
+        if (o.l_max < 0) hk::fail(HK_EINVAL, "l_max=%d must be >= 0", o.l_max);
+        if (o.query_group < 0 || o.series_tile < 0) hk::fail(HK_EINVAL, "tile sizes must be >= 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        idx->stream = s;
+        hk::DevBuf<float> tmp;
+        const float *Qd = device_view(Q, (size_t)nq * idx->n, s, tmp);
+        hk::check_finite(Qd, (int64_t)nq * idx->n, s, "Q");
+        hk::run_query(idx, Qd, nq, k, o, s, out_ids, out_dist, stats);
+    });
+}
+
+int hk_scan_knn(const float *X, int64_t N, int32_t n, const float *Q, int32_t nq, int32_t k,
+                void *stream, int64_t *out_ids, float *out_dist) {
+    return guard([&] {
+        if (!X || !Q || !out_ids || !out_dist) hk::fail(HK_EINVAL, "NULL argument");
+        if (N < 1 || N > 0x7fffffffLL) hk::fail(HK_EINVAL, "N=%lld must be in [1, 2^31-1]", (long long)N);
+        check_len(n);
+        if (nq < 1) hk::fail(HK_EINVAL, "nq=%d must be >= 1", nq);
+        if (k < 1 || k > HK_MAX_K || (int64_t)k > N)
+            hk::fail(HK_EINVAL, "k=%d must be in [1, min(N, %d)]", k, HK_MAX_K);
+        cudaStream_t s = (cudaStream_t)stream;
+        hk::DevBuf<float> tx, tq;
+        const float *Xd = device_view(X, (size_t)N * n, s, tx);
+        const float *Qd = device_view(Q, (size_t)nq * n, s, tq);
+        hk::check_finite(Xd, N * (int64_t)n, s, "X");
+        hk::check_finite(Qd, nq * (int64_t)n, s, "Q");
+        hk::run_scan(Xd, N, n, Qd, nq, k, s, out_ids, out_dist);
+    });
+}
+
+int hk_index_export(const hk_index *idx, int64_t *perm, int64_t *leaf_off, int32_t *leaf_nseg,
+                    int32_t *seg_end, double *env, uint8_t *sax) {
+    return guard([&] {
+        if (!idx) hk::fail(HK_EINVAL, "idx is NULL");
+        const int64_t L = idx->L, N = idx->N;
+        if (perm) HK_CHECK_CUDA(cudaMemcpy(perm, idx->perm.p, N * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        if (leaf_off) std::memcpy(leaf_off, idx->h_leaf_off.data(), (L + 1) * sizeof(int64_t));
+        if (leaf_nseg) std::memcpy(leaf_nseg, idx->h_leaf_nseg.data(), L * sizeof(int32_t));
+        if (seg_end) std::memcpy(seg_end, idx->h_seg_end.data(), L * hk::kMaxSeg * sizeof(int32_t));
+        if (env)
+            HK_CHECK_CUDA(cudaMemcpy(env, idx->env.p, L * hk::kMaxSeg * 4 * sizeof(double),
+                                     cudaMemcpyDeviceToHost));
+        if (sax)
+            HK_CHECK_CUDA(cudaMemcpy(sax, idx->sax.p, N * hk::kWord, cudaMemcpyDeviceToHost));
+    });
+}
+
+int hk_debug_lb_eapca(hk_index *idx, const float *Q, int32_t nq, double *out) {
+    return guard([&] {
+        if (!idx || !Q || !out || nq < 1) hk::fail(HK_EINVAL, "bad argument");
+        hk::DevBuf<float> tmp;
+        const float *Qd = device_view(Q, (size_t)nq * idx->n, idx->stream, tmp);
+        hk::debug_lb_eapca(idx, Qd, nq, out);
+    });
+}
+
+int hk_debug_lb_sax(hk_index *idx, const float *Q, int32_t nq, float *out) {
+    return guard([&] {
+        if (!idx || !Q || !out || nq < 1) hk::fail(HK_EINVAL, "bad argument");
+        hk::DevBuf<float> tmp;
+        const float *Qd = device_view(Q, (size_t)nq * idx->n, idx->stream, tmp);
+        hk::debug_lb_sax(idx, Qd, nq, out);
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Internal declarations of the GB300 Hercules library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hercules_gb300.h"
+
+namespace hk {
+
+constexpr int kMaxSeg = 64;          // segments a leaf may have (V-splits stop here)
+constexpr int kRootSegments = 4;     // root segmentation: 4 equal segments
+constexpr int kWord = HK_ISAX_SEGMENTS;
+constexpr int kAlpha = HK_ISAX_ALPHABET;
+constexpr int kDefaultEvalCap = 4096;
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void fail(int code, const char *fmt, ...);
+void set_last_error(int code, const std::string &msg);
+void clear_last_error();
+
+#define HK_CHECK_CUDA(call)                                                    \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess)                                                 \
+            ::hk::fail(e_ == cudaErrorMemoryAllocation ? HK_ENOMEM : HK_ECUDA, \
+                       "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                       __FILE__, __LINE__);                                    \
+    } while (0)
+
+#define HK_CHECK_LAUNCH() HK_CHECK_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- device memory
+// Owning device buffer.  cudaMalloc/cudaFree: cudaFree waits for the device,
+// so a buffer can be released whichever stream last used it.
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept { *this = std::move(o); }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t count, cudaStream_t = nullptr) {
+        release();
+        if (count == 0) return;
+        HK_CHECK_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+        n = count;
+    }
+    // Grow to at least count elements (contents are not kept).
+    void reserve(size_t count, cudaStream_t s = nullptr) {
+        if (count > n || p == nullptr) alloc(count < 1 ? 1 : count, s);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// ---------------------------------------------------------------- host helpers
+bool is_device_ptr(const void *p);
+void isax_breakpoints(float out[255]);   // library's own computation
+
+// Exclusive scan of int32 counts on the device: out[i] = sum_{j<i} in[j],
+// out[n] = total.  Stream-ordered, no host synchronisation.
+void exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s,
+                        DevBuf<int32_t> &scratch);
+void exclusive_scan_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s,
+                        DevBuf<int64_t> &scratch);
+
+// ---------------------------------------------------------------- query workspace
+struct Workspace {
+    DevBuf<float> Q;            // nq * n
+    DevBuf<double> qseg;        // nq * S * 2  (mu, sd) per distinct segment
+    DevBuf<float> sax_tab;      // nq * 16 * 256 LB_SAX table (rounded down)
+    DevBuf<double> lb;          // nq * L
+    DevBuf<uint32_t> U;         // nq   bound on the k-th distance (float bits)
+    DevBuf<uint8_t> qmode;      // nq   bit0: LB_SAX filter on
+    DevBuf<int32_t> qcand;      // nq   candidate leaves per query
+    DevBuf<uint8_t> mask;       // L * nq  (leaf-major): 1 approx, 2 candidate
+    DevBuf<int32_t> leaf_qcnt;  // L
+    DevBuf<int32_t> leaf_qoff;  // L + 1
+    DevBuf<int32_t> leaf_q;     // <= L * nq
+    DevBuf<int32_t> leaf_items; // L
+    DevBuf<int64_t> item_off;   // L + 1
+    DevBuf<int32_t> counters;   // scan work counter and flags
+    DevBuf<float> pool_d;       // nq * C
+    DevBuf<int32_t> pool_p;     // nq * C
+    DevBuf<int32_t> pool_cnt;   // nq
+    DevBuf<int32_t> qflag;      // nq   bit0 overflow
+    DevBuf<double> rs_d;        // nq * C  binary64 rescored distances
+    DevBuf<int64_t> stats;      // counters (hk_query_stats layout)
+    DevBuf<int32_t> scan_tmp32;
+    DevBuf<int64_t> scan_tmp64;
+    DevBuf<int64_t> out_ids;    // nq * k
+    DevBuf<float> out_dist;     // nq * k
+    DevBuf<int32_t> approx;     // nq * A
+};
+
+// Device view of a collection laid out by leaves (an index, or a plain
+// collection seen as one leaf for the exhaustive scan).
+struct LeafView {
+    const float *X = nullptr;       // N * n, leaf order
+    const int64_t *perm = nullptr;  // position -> original id (nullptr: identity)
+    const uint8_t *sax = nullptr;   // N * 16 (nullptr: no LB_SAX)
+    const int64_t *leaf_off = nullptr;  // L + 1
+    int64_t N = 0;
+    int n = 0;
+    int64_t L = 0;
+};
+
+}  // namespace hk
+
+// ---------------------------------------------------------------- the index
+struct hk_index {
+    cudaStream_t stream = nullptr;
+    int64_t N = 0;
+    int n = 0;
+    int tau = 0;
+    int eval_cap = 0;
+    int64_t L = 0;
+    int max_m = 0;
+    int depth = 0;
+    int64_t S = 0;   // distinct segments over all leaves
+
+    hk::DevBuf<float> X;           // N*n  leaf order
+    hk::DevBuf<int64_t> perm;      // N
+    hk::DevBuf<uint8_t> sax;       // N*16
+    hk::DevBuf<int64_t> leaf_off;  // L+1
+    hk::DevBuf<int32_t> leaf_nseg; // L
+    hk::DevBuf<int32_t> leaf_seg;  // L*kMaxSeg distinct-segment ids
+    hk::DevBuf<double> env;        // L*kMaxSeg*4
+    hk::DevBuf<int32_t> seg_ab;    // S*2  (a, b)
+    hk::DevBuf<float> bp;          // 255 breakpoints
+
+    std::vector<int64_t> h_leaf_off;
+    std::vector<int32_t> h_leaf_nseg;
+    std::vector<int32_t> h_seg_end;   // L*kMaxSeg
+
+    hk::Workspace ws;
+};
+
+namespace hk {
+// Build (hk_build.cu)
+void build_index(hk_index *idx, const float *X, int64_t N, int n, const hk_build_opts &o,
+                 cudaStream_t s);
+// Query (hk_query.cu)
+void run_query(hk_index *idx, const float *Qdev, int nq, int k, const hk_query_opts &o,
+               cudaStream_t s, int64_t *out_ids_host_or_dev, float *out_dist_host_or_dev,
+               hk_query_stats *stats);
+void run_scan(const float *Xdev, int64_t N, int n, const float *Qdev, int nq, int k,
+              cudaStream_t s, int64_t *out_ids, float *out_dist);
+void debug_lb_eapca(hk_index *idx, const float *Qdev, int nq, double *out_host);
+void debug_lb_sax(hk_index *idx, const float *Qdev, int nq, float *out_host);
+void check_finite(const float *p, int64_t count, cudaStream_t s, const char *what);
+}  // namespace hk

@@ -1,0 +1,1129 @@
+// Exact k-NN query answering on the GPU (Sec. 3.4, Algorithm Exact-kNN).
+//
+// A batch of queries is answered together.  Per query the steps are the
+// paper's: the approximate search scans the leaves with the smallest
+// LB_EAPCA (Approx-kNN; with lower bounds that grow from parent to child,
+// best-first order over the tree is ascending leaf LB order) and sets BSF_k;
+// leaves whose LB_EAPCA cannot beat BSF_k are pruned (FindCandidateLeaves);
+// within the remaining leaves LB_SAX prunes series (CSWorker) unless pruning
+// was too weak (EAPCA_TH, then the leaves are scanned whole as in the
+// skip-sequential scan); the rest get their squared Euclidean distance with
+// early abandoning and update the k best (CRWorker).
+//
+// GPU organisation: work is leaf-major.  A work item is one tile of a leaf's
+// series and a group of up to G queries for which that leaf is a candidate;
+// its CTA reads each series once for all of them.  Each item keeps, per
+// query, a sorted list of its best candidates in shared memory and publishes
+// them to a per-query pool at the end; the k-th entry of a list bounds the
+// query's k-th distance, so it tightens a global per-query bound U (atomicMin)
+// that every later item prunes and abandons against.
+//
+// Exactness.  Distances here are float32; the answer is ranked by the
+// binary64 squared distance summed in index order (ties to the lower id).
+// With rho >= gamma_{n+2} = (n+2)u/(1-(n+2)u), u = 2^-24, every float32
+// distance or partial sum s of a true (real) value D satisfies
+// s <= D(1+rho) and D <= s(1+rho).  U is always an upper bound on the true
+// k-th distance (the (1+rho)-inflated k-th float32 distance of some k
+// series), and a series is dropped only when a certified lower bound on its
+// distance (LB_EAPCA, LB_SAX, or a partial sum) exceeds U, or when its
+// float32 distance exceeds T(U) = U(1+rho) rounded up.  The final step
+// recomputes in binary64 every pooled candidate at or below T(U_final) and
+// ranks them by (binary64 distance, id).  If a list or pool overflows (more
+// near-ties than it holds), that query is redone by an exhaustive collection
+// of every series at or below T(U_final).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hk_device.cuh"
+#include "hk_internal.cuh"
+
+namespace hk {
+namespace {
+
+constexpr int kBT = 256;       // scan CTA threads = series per chunk
+constexpr int kSlack = 32;     // room for near-ties beyond k in an item list
+constexpr int kMaxG = 8;
+constexpr int kStatSlots = 16;
+constexpr int kAmax = 256;     // most leaves the approximate step visits
+
+enum StatIdx {
+    ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_APPROX, ST_LEAVES_CAND, ST_SERIES_CAND,
+    ST_SAX_PRUNED, ST_ABANDONED, ST_FULL, ST_POINTS, ST_RESCORED, ST_FALLBACK,
+    ST_ITEMS, ST_SKIPSEQ
+};
+
+struct ScanArgs {
+    LeafView v;
+    const float *Q;
+    int nq;
+    const float *sax_tab;      // nq*16*256 or nullptr
+    const uint8_t *qmode;      // nq (bit0: LB_SAX on) or nullptr
+    const double *lb;          // nq*L or nullptr
+    uint32_t *U;               // nq float bits
+    const int32_t *leaf_qoff;  // L+1
+    const int32_t *leaf_q;
+    const int64_t *item_off;   // L+1
+    int32_t *work_ctr;
+    int S_T;
+    int k;
+    int cap;                   // list capacity
+    int p2;                    // sort length (power of two >= cap + kBT)
+    float rho;
+    float *pool_d;
+    int32_t *pool_p;
+    int32_t *pool_cnt;
+    int pool_C;
+    int32_t *qflag;
+    long long *stats;
+    int use_sax;
+};
+
+__device__ __forceinline__ float upper_f(float d, float rho) { return __fmul_ru(d, 1.0f + rho); }
+
+// --------------------------------------------------------------------------
+// a1: query preparation.  Per query: mean and std of every distinct leaf
+// segment (binary64, the build's exact definition), PAA over 16 segments, and
+// the LB_SAX table T[i][s] = (n/16) dist(PAA_i, cell s)^2 rounded down.
+__global__ void k_qprep(const float *__restrict__ Q, int n, const int32_t *__restrict__ seg_ab,
+                        int64_t S, const float *__restrict__ bp, double *__restrict__ qseg,
+                        float *__restrict__ tab) {
+    extern __shared__ float qs[];
+    __shared__ double paa[kWord];
+    __shared__ float bps[255];
+    const int q = blockIdx.x;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) qs[j] = Q[(int64_t)q * n + j];
+    for (int j = threadIdx.x; j < 255; j += blockDim.x) bps[j] = bp[j];
+    __syncthreads();
+    if (qseg) {
+        for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+            double mu, sd;
+            seg_stats64(qs, seg_ab[2 * s], seg_ab[2 * s + 1], mu, sd);
+            qseg[((int64_t)q * S + s) * 2] = mu;
+            qseg[((int64_t)q * S + s) * 2 + 1] = sd;
+        }
+    }
+    if (tab) {
+        const int l = n / kWord;
+        if (threadIdx.x < kWord)
+            paa[threadIdx.x] = seg_mean64(qs, threadIdx.x * l, (threadIdx.x + 1) * l);
+        __syncthreads();
+        const double w = (double)l;
+        for (int t = threadIdx.x; t < kWord * kAlpha; t += blockDim.x) {
+            const int i = t / kAlpha, sym = t % kAlpha;
+            const double lo = sym == 0 ? -INFINITY : (double)bps[sym - 1];
+            const double hi = sym == kAlpha - 1 ? INFINITY : (double)bps[sym];
+            const double d = dist_to_range64(paa[i], lo, hi);
+            tab[(int64_t)q * kWord * kAlpha + t] = __double2float_rd(__dmul_rn(w, __dmul_rn(d, d)));
+        }
+    }
+}
+
+// a2: LB_EAPCA of every query to every leaf synopsis (binary64, the segment
+// sum in segment order, exactly the definition).
+__global__ void k_lb_eapca(const double *__restrict__ qseg, int64_t S,
+                           const int32_t *__restrict__ leaf_nseg, const int32_t *__restrict__ leaf_seg,
+                           const int32_t *__restrict__ seg_ab, const double *__restrict__ env,
+                           int64_t L, int nq, double *__restrict__ lb) {
+    const int64_t leaf = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (leaf >= L) return;
+    const int m = leaf_nseg[leaf];
+    for (int q = blockIdx.y; q < nq; q += gridDim.y) {
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j) {
+        const int sid = leaf_seg[leaf * kMaxSeg + j];
+        const double l = (double)(seg_ab[2 * sid + 1] - seg_ab[2 * sid]);
+        const double mu = qseg[((int64_t)q * S + sid) * 2];
+        const double sd = qseg[((int64_t)q * S + sid) * 2 + 1];
+        const double *z = env + (leaf * kMaxSeg + j) * 4;
+        const double dm = dist_to_range64(mu, z[0], z[1]);
+        const double ds = dist_to_range64(sd, z[2], z[3]);
+        const double t = __dadd_rn(__dmul_rn(dm, dm), __dmul_rn(ds, ds));
+        acc = __dadd_rn(acc, __dmul_rn(l, t));
+    }
+    lb[(int64_t)q * L + leaf] = acc;
+    }
+}
+
+// Certified lower value of a binary64 LB (absorbs its rounding).
+__device__ __forceinline__ double lb_lower(double lb) { return __dmul_rd(lb, 1.0 - 0x1p-40); }
+
+// a3 (selection): the leaves the approximate search visits: ascending
+// (LB_EAPCA, leaf) until at least l_max leaves and at least k series.
+__global__ void k_approx_select(const double *__restrict__ lb, int64_t L,
+                                const int64_t *__restrict__ leaf_off, int l_max, int k, int nq,
+                                int amax, int32_t *__restrict__ approx, int32_t *__restrict__ napprox,
+                                uint8_t *__restrict__ mask) {
+    __shared__ double bd[32];
+    __shared__ long long bl[32];
+    __shared__ int chosen[kAmax];
+    __shared__ int nch;
+    __shared__ long long covered;
+    const int q = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) { nch = 0; covered = 0; }
+    __syncthreads();
+    for (;;) {
+        if (!(nch < amax && (nch < l_max || covered < k))) break;
+        double best = INFINITY;
+        long long bleaf = -1;
+        for (int64_t f = threadIdx.x; f < L; f += blockDim.x) {
+            bool taken = false;
+            for (int c = 0; c < nch; ++c) taken |= (chosen[c] == (int)f);
+            if (taken) continue;
+            const double v = lb[(int64_t)q * L + f];
+            if (bleaf < 0 || v < best || (v == best && f < bleaf)) { best = v; bleaf = f; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const long long ol = __shfl_xor_sync(0xffffffffu, bleaf, o);
+            if (ol >= 0 && (bleaf < 0 || ov < best || (ov == best && ol < bleaf))) { best = ov; bleaf = ol; }
+        }
+        if (lane == 0) { bd[warp] = best; bl[warp] = bleaf; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = INFINITY;
+            long long f = -1;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (bl[w] >= 0 && (f < 0 || bd[w] < b || (bd[w] == b && bl[w] < f))) { b = bd[w]; f = bl[w]; }
+            if (f < 0) {
+                covered = (long long)1 << 62;   // nothing left: stop
+                chosen[nch] = -1;
+            } else {
+                chosen[nch] = (int)f;
+                approx[(int64_t)q * amax + nch] = (int)f;
+                mask[f * nq + q] = 1;
+                covered += leaf_off[f + 1] - leaf_off[f];
+                nch = nch + 1;
+            }
+        }
+        __syncthreads();
+        if (covered >= ((long long)1 << 62)) break;
+    }
+    if (threadIdx.x == 0) napprox[q] = nch;
+}
+
+// a4: leaf prune (FindCandidateLeaves): a leaf stays a candidate for a query
+// unless its certified LB_EAPCA exceeds U.
+__global__ void k_mask_candidates(const double *__restrict__ lb, int64_t L, int nq,
+                                  const uint32_t *__restrict__ U, int noprune,
+                                  uint8_t *__restrict__ mask, int32_t *__restrict__ qcand) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L * (int64_t)nq) return;
+    const int64_t leaf = t / nq;
+    const int q = (int)(t % nq);
+    if (mask[t] != 0) return;
+    bool cand = noprune != 0;
+    if (!cand) {
+        const double u = (double)__uint_as_float(U[q]);
+        cand = !(lb_lower(lb[(int64_t)q * L + leaf]) > u);
+    }
+    if (cand) {
+        mask[t] = 2;
+        atomicAdd(&qcand[q], 1);
+    }
+}
+
+// Per-query mode: LB_SAX filter on unless disabled or EAPCA pruning fell
+// below EAPCA_TH (then the candidate leaves are scanned whole).
+__global__ void k_qmode(const int32_t *__restrict__ qcand, int64_t L, int nq, float eapca_th,
+                        int nosax, int nothresh, uint8_t *__restrict__ qmode,
+                        long long *__restrict__ stats) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double pr = 1.0 - (double)qcand[q] / (double)L;
+    int on = nosax ? 0 : 1;
+    if (on && !nothresh && pr < (double)eapca_th) {
+        on = 0;
+        stat_add(&stats[ST_SKIPSEQ], 1);
+    }
+    qmode[q] = (uint8_t)on;
+    stat_add(&stats[ST_LEAVES_CAND], qcand[q]);
+}
+
+// Leaf-major lists: per leaf, the queries whose mask equals v, and the number
+// of work items (query groups x series tiles).
+__global__ void k_leaf_count(const uint8_t *__restrict__ mask, int nq, uint8_t v,
+                             const int64_t *__restrict__ leaf_off, int G, int S_T,
+                             int32_t *__restrict__ qcnt, int32_t *__restrict__ items) {
+    __shared__ int red[32];
+    const int64_t leaf = blockIdx.x;
+    int c = 0;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) c += mask[leaf * nq + q] == v;
+    c = warp_sum_i(c);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        qcnt[leaf] = tot;
+        const int64_t size = leaf_off[leaf + 1] - leaf_off[leaf];
+        const int64_t tiles = (size + S_T - 1) / S_T;
+        items[leaf] = tot == 0 ? 0 : (int32_t)(((tot + G - 1) / G) * tiles);
+    }
+}
+
+__global__ void k_leaf_fill(const uint8_t *__restrict__ mask, int nq, uint8_t v,
+                            const int32_t *__restrict__ qoff, int32_t *__restrict__ leaf_q) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int64_t leaf = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = qoff[leaf];
+    __syncthreads();
+    for (int q0 = 0; q0 < nq; q0 += blockDim.x) {
+        const int q = q0 + threadIdx.x;
+        const bool hit = q < nq && mask[leaf * nq + q] == v;
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+        if (hit) leaf_q[base + off + __popc(bal & ((1u << lane) - 1))] = q;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < nw; ++w) tot += wsum[w];
+            base += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------------------
+// a5-a7: the scan.  One CTA per work item at a time (persistent grid).
+template <int G>
+__global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = A.v.n;
+    float *q_s = reinterpret_cast<float *>(smem_raw);                 // G*n
+    float *tab_s = q_s + G * n;                                       // G*4096 if use_sax
+    float *stage_d = tab_s + (A.use_sax ? G * kWord * kAlpha : 0);    // G*kBT
+    int32_t *stage_p = reinterpret_cast<int32_t *>(stage_d + G * kBT);
+    float *list_d = reinterpret_cast<float *>(stage_p + G * kBT);     // G*p2
+    int32_t *list_p = reinterpret_cast<int32_t *>(list_d + G * A.p2);
+
+    __shared__ int64_t s_item;
+    __shared__ int s_qid[G];
+    __shared__ float s_U[G], s_T[G], s_Tsax[G];
+    __shared__ int s_alive[G], s_sax[G];
+    __shared__ int s_stage[G], s_list[G];
+    __shared__ int64_t s_s0, s_s1;
+    __shared__ int s_gq, s_leaf;
+    __shared__ long long s_cnt[4];   // sax pruned, abandoned, full, points
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t total = A.item_off[A.v.L];
+    const float rho = A.rho;
+    long long my_sax = 0, my_ab = 0, my_full = 0, my_pts = 0;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(A.work_ctr, 1);
+        __syncthreads();
+        const int64_t it = s_item;
+        if (it >= total) break;
+        if (tid == 0) {
+            const int leaf = find_segment<int64_t>(A.item_off, (int)A.v.L + 1, it);
+            // skip leaves with no items (equal offsets): find the last leaf
+            // whose offset <= it, which find_segment already returns
+            const int64_t local = it - A.item_off[leaf];
+            const int nql = A.leaf_qoff[leaf + 1] - A.leaf_qoff[leaf];
+            const int ngroups = (nql + G - 1) / G;
+            const int64_t tile = local / ngroups;
+            const int grp = (int)(local % ngroups);
+            const int64_t lo = A.v.leaf_off[leaf], hi = A.v.leaf_off[leaf + 1];
+            s_s0 = lo + tile * A.S_T;
+            s_s1 = min(s_s0 + (int64_t)A.S_T, hi);
+            s_gq = min(G, nql - grp * G);
+            s_leaf = leaf;
+            for (int g = 0; g < G; ++g) {
+                s_alive[g] = 0;
+                if (g < s_gq) {
+                    const int q = A.leaf_q[A.leaf_qoff[leaf] + grp * G + g];
+                    s_qid[g] = q;
+                    const float u = __uint_as_float(A.U[q]);
+                    s_U[g] = u;
+                    bool alive = true;
+                    if (A.lb) alive = !(lb_lower(A.lb[(int64_t)q * A.v.L + leaf]) > (double)u);
+                    s_alive[g] = alive;
+                    s_sax[g] = (A.use_sax && A.qmode && (A.qmode[q] & 1)) ? 1 : 0;
+                    s_T[g] = __fmul_ru(u, 1.0f + rho);
+                    s_Tsax[g] = __fmul_ru(u, 1.0f + 0x1p-18f);
+                }
+                s_stage[g] = 0;
+                s_list[g] = 0;
+            }
+        }
+        __syncthreads();
+        const int gq = s_gq;
+        unsigned alive_mask = 0, sax_mask = 0;
+        for (int g = 0; g < gq; ++g) {
+            if (s_alive[g]) alive_mask |= 1u << g;
+            if (s_alive[g] && s_sax[g]) sax_mask |= 1u << g;
+        }
+        if (!alive_mask) {
+            __syncthreads();
+            continue;
+        }
+        // stage the queries (and LB_SAX tables) in shared memory
+        for (int g = 0; g < gq; ++g) {
+            if (!(alive_mask >> g & 1)) continue;
+            const float4 *src = reinterpret_cast<const float4 *>(A.Q + (int64_t)s_qid[g] * n);
+            float4 *dst = reinterpret_cast<float4 *>(q_s + g * n);
+            for (int j = tid; j < (n >> 2); j += kBT) dst[j] = src[j];
+            if (sax_mask >> g & 1) {
+                const float4 *ts = reinterpret_cast<const float4 *>(A.sax_tab + (int64_t)s_qid[g] * kWord * kAlpha);
+                float4 *td = reinterpret_cast<float4 *>(tab_s + g * kWord * kAlpha);
+                for (int j = tid; j < kWord * kAlpha / 4; j += kBT) td[j] = ts[j];
+            }
+        }
+        __syncthreads();
+
+        const int64_t s0 = s_s0, s1 = s_s1;
+        for (int64_t c0 = s0; c0 < s1; c0 += kBT) {
+            const int64_t s = c0 + tid;
+            if (s < s1) {
+                unsigned act = alive_mask;
+                float T[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) T[g] = s_T[g];
+                if (sax_mask) {
+                    const uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(A.v.sax) + s);
+                    const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        if (!(sax_mask >> g & 1)) continue;
+                        const float *tg = tab_s + g * kWord * kAlpha;
+                        float lbs = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < kWord; ++i)
+                            lbs += tg[i * kAlpha + ((wv[i >> 2] >> ((i & 3) * 8)) & 0xff)];
+                        if (lbs > s_Tsax[g]) {
+                            act &= ~(1u << g);
+                            ++my_sax;
+                        }
+                    }
+                }
+                float acc[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc[g] = 0.0f;
+                const float4 *xr = reinterpret_cast<const float4 *>(A.v.X + s * n);
+                for (int j = 0; j < n && act; j += 16) {
+                    const float4 x0 = __ldg(xr + (j >> 2) + 0);
+                    const float4 x1 = __ldg(xr + (j >> 2) + 1);
+                    const float4 x2 = __ldg(xr + (j >> 2) + 2);
+                    const float4 x3 = __ldg(xr + (j >> 2) + 3);
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        if (!(act >> g & 1)) continue;
+                        const float4 *qv = reinterpret_cast<const float4 *>(q_s + g * n + j);
+                        const float4 q0 = qv[0], q1 = qv[1], q2 = qv[2], q3 = qv[3];
+                        float a = acc[g], d;
+                        d = q0.x - x0.x; a = fmaf(d, d, a);
+                        d = q0.y - x0.y; a = fmaf(d, d, a);
+                        d = q0.z - x0.z; a = fmaf(d, d, a);
+                        d = q0.w - x0.w; a = fmaf(d, d, a);
+                        d = q1.x - x1.x; a = fmaf(d, d, a);
+                        d = q1.y - x1.y; a = fmaf(d, d, a);
+                        d = q1.z - x1.z; a = fmaf(d, d, a);
+                        d = q1.w - x1.w; a = fmaf(d, d, a);
+                        d = q2.x - x2.x; a = fmaf(d, d, a);
+                        d = q2.y - x2.y; a = fmaf(d, d, a);
+                        d = q2.z - x2.z; a = fmaf(d, d, a);
+                        d = q2.w - x2.w; a = fmaf(d, d, a);
+                        d = q3.x - x3.x; a = fmaf(d, d, a);
+                        d = q3.y - x3.y; a = fmaf(d, d, a);
+                        d = q3.z - x3.z; a = fmaf(d, d, a);
+                        d = q3.w - x3.w; a = fmaf(d, d, a);
+                        acc[g] = a;
+                        my_pts += 16;
+                        if (a > T[g]) {
+                            act &= ~(1u << g);
+                            ++my_ab;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    if (!(act >> g & 1)) continue;
+                    ++my_full;
+                    const int slot = atomicAdd(&s_stage[g], 1);
+                    stage_d[g * kBT + slot] = acc[g];
+                    stage_p[g * kBT + slot] = (int32_t)s;
+                }
+            }
+            __syncthreads();
+            // merge: warp g owns query g's list
+            if (warp < gq && (alive_mask >> warp & 1)) {
+                const int g = warp;
+                float *ld = list_d + g * A.p2;
+                int32_t *lp = list_p + g * A.p2;
+                const int sc = s_stage[g];
+                const int cnt = s_list[g];
+                float U = s_U[g];
+                const float ug = __uint_as_float(A.U[s_qid[g]]);
+                U = fminf(U, ug);
+                if (sc > 0) {
+                    for (int i = lane; i < sc; i += 32) {
+                        ld[cnt + i] = stage_d[g * kBT + i];
+                        lp[cnt + i] = stage_p[g * kBT + i];
+                    }
+                    const int tot = cnt + sc;
+                    int P = 32;
+                    while (P < tot) P <<= 1;
+                    for (int i = tot + lane; i < P; i += 32) {
+                        ld[i] = INFINITY;
+                        lp[i] = 0x7fffffff;
+                    }
+                    __syncwarp();
+                    for (int size = 2; size <= P; size <<= 1) {
+                        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                            for (int i = lane; i < (P >> 1); i += 32) {
+                                const int lo = 2 * stride * (i / stride) + (i % stride);
+                                const int hi = lo + stride;
+                                const bool asc = (lo & size) == 0;
+                                const float a = ld[lo], b = ld[hi];
+                                const int32_t pa = lp[lo], pb = lp[hi];
+                                const bool gt = (a > b) || (a == b && pa > pb);
+                                if (gt == asc) {
+                                    ld[lo] = b; ld[hi] = a;
+                                    lp[lo] = pb; lp[hi] = pa;
+                                }
+                            }
+                            __syncwarp();
+                        }
+                    }
+                    if (tot >= A.k) U = fminf(U, upper_f(ld[A.k - 1], rho));
+                    const float T = __fmul_ru(U, 1.0f + rho);
+                    // keep the prefix with d <= T
+                    int keep = 0;
+                    for (int i = lane; i < tot; i += 32) keep += (ld[i] <= T) ? 1 : 0;
+                    keep = warp_sum_i(keep);
+                    if (keep > A.cap) {
+                        if (lane == 0) atomicOr(&A.qflag[s_qid[g]], 1);
+                        keep = A.cap;
+                    }
+                    if (lane == 0) s_list[g] = keep;
+                }
+                if (lane == 0) {
+                    s_U[g] = U;
+                    s_T[g] = __fmul_ru(U, 1.0f + rho);
+                    s_Tsax[g] = __fmul_ru(U, 1.0f + 0x1p-18f);
+                    s_stage[g] = 0;
+                }
+            }
+            __syncthreads();
+        }
+        // publish: entries at or below T(min(U_item, U_global)), then tighten U
+        if (warp < gq && (alive_mask >> warp & 1)) {
+            const int g = warp;
+            const int q = s_qid[g];
+            const float Uf = fminf(s_U[g], __uint_as_float(A.U[q]));
+            const float T = __fmul_ru(Uf, 1.0f + rho);
+            const float *ld = list_d + g * A.p2;
+            const int32_t *lp = list_p + g * A.p2;
+            const int cnt = s_list[g];
+            int e = 0;
+            for (int i = lane; i < cnt; i += 32) e += (ld[i] <= T) ? 1 : 0;
+            e = warp_sum_i(e);
+            int base = 0;
+            if (lane == 0 && e > 0) base = atomicAdd(&A.pool_cnt[q], e);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int ew = e;
+            if (base + e > A.pool_C) {
+                ew = max(0, A.pool_C - base);
+                if (lane == 0) atomicOr(&A.qflag[q], 1);
+            }
+            for (int i = lane; i < ew; i += 32) {
+                A.pool_d[(int64_t)q * A.pool_C + base + i] = ld[i];
+                A.pool_p[(int64_t)q * A.pool_C + base + i] = lp[i];
+            }
+            if (lane == 0) atomicMin(&A.U[q], __float_as_uint(s_U[g]));
+        }
+        __syncthreads();
+    }
+    // statistics
+    my_sax = warp_sum_ll(my_sax);
+    my_ab = warp_sum_ll(my_ab);
+    my_full = warp_sum_ll(my_full);
+    my_pts = warp_sum_ll(my_pts);
+    if (lane == 0) {
+        stat_add(&A.stats[ST_SAX_PRUNED], my_sax);
+        stat_add(&A.stats[ST_ABANDONED], my_ab);
+        stat_add(&A.stats[ST_FULL], my_full);
+        stat_add(&A.stats[ST_POINTS], my_pts);
+    }
+}
+
+// U = min(U, (1+rho) x k-th smallest pooled float32 distance).
+__global__ void k_pool_kth(const float *__restrict__ pool_d, const int32_t *__restrict__ pool_cnt,
+                           int C, int k, float rho, uint32_t *__restrict__ U) {
+    __shared__ int red[32];
+    const int q = blockIdx.x;
+    const int cnt = min(pool_cnt[q], C);
+    if (cnt < k) return;
+    const float *d = pool_d + (int64_t)q * C;
+    uint32_t lo = 0, hi = 0x7f800000u;
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        int c = 0;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) c += __float_as_uint(d[i]) <= mid;
+        c = warp_sum_i(c);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        __syncthreads();
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        __syncthreads();
+        if (tot >= k) hi = mid; else lo = mid + 1;
+    }
+    if (threadIdx.x == 0) atomicMin(&U[q], __float_as_uint(upper_f(__uint_as_float(lo), rho)));
+}
+
+// a8: binary64 rescore of every pooled candidate at or below T(U) and the
+// final top-k by (binary64 distance, original id).
+__global__ void k_final(const float *__restrict__ Q, const float *__restrict__ X, int n,
+                        const int64_t *__restrict__ perm, const float *__restrict__ pool_d,
+                        const int32_t *__restrict__ pool_p, const int32_t *__restrict__ pool_cnt,
+                        int C, const uint32_t *__restrict__ U, const int32_t *__restrict__ qflag,
+                        int k, float rho, double *__restrict__ rs, int64_t *__restrict__ out_ids,
+                        float *__restrict__ out_dist, long long *__restrict__ stats,
+                        int32_t *__restrict__ err, const int32_t *__restrict__ qsel) {
+    __shared__ double bd[32];
+    __shared__ long long bi[32];
+    __shared__ int be[32];
+    const int q = qsel ? qsel[blockIdx.x] : blockIdx.x;
+    const int64_t slot = qsel ? blockIdx.x : q;   // row of the pool for this block
+    if (qflag && (qflag[q] & 1)) return;
+    const int cnt = min(pool_cnt[slot], C);
+    const float T = __fmul_ru(__uint_as_float(U[q]), 1.0f + rho);
+    const float *pd = pool_d + slot * C;
+    const int32_t *pp = pool_p + slot * C;
+    double *r = rs + slot * C;
+    int resc = 0;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        double v = INFINITY;
+        if (pd[i] <= T) {
+            const int64_t pos = pp[i];
+            v = dist2_64(Q + (int64_t)q * n, X + pos * n, n);
+            ++resc;
+        }
+        r[i] = v;
+    }
+    resc = warp_sum_i(resc);
+    if ((threadIdx.x & 31) == 0 && resc) stat_add(&stats[ST_RESCORED], resc);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = 0; t < k; ++t) {
+        double b = INFINITY;
+        long long id = -1;
+        int e = -1;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const double v = r[i];
+            if (v == INFINITY) continue;
+            const long long pid = perm ? perm[pp[i]] : (long long)pp[i];
+            if (e < 0 || v < b || (v == b && pid < id)) { b = v; id = pid; e = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, b, o);
+            const long long oid = __shfl_xor_sync(0xffffffffu, id, o);
+            const int oe = __shfl_xor_sync(0xffffffffu, e, o);
+            if (oe >= 0 && (e < 0 || ov < b || (ov == b && oid < id))) { b = ov; id = oid; e = oe; }
+        }
+        if (lane == 0) { bd[warp] = b; bi[warp] = id; be[warp] = e; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bb = INFINITY;
+            long long ii = -1;
+            int ee = -1;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (be[w] >= 0 && (ee < 0 || bd[w] < bb || (bd[w] == bb && bi[w] < ii))) {
+                    bb = bd[w]; ii = bi[w]; ee = be[w];
+                }
+            if (ee < 0) {
+                atomicOr(err, 1);
+                out_ids[(int64_t)q * k + t] = -1;
+                out_dist[(int64_t)q * k + t] = INFINITY;
+            } else {
+                out_ids[(int64_t)q * k + t] = ii;
+                out_dist[(int64_t)q * k + t] = __double2float_rn(__dsqrt_rn(bb));
+                r[ee] = INFINITY;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Fallback: every series of the collection whose float32 distance to query q
+// is at or below T(U[q]) (pass 0 counts, pass 1 writes).
+__global__ void k_collect(const float *__restrict__ Q, int q, const float *__restrict__ X, int n,
+                          int64_t N, float T, int pass, int32_t *__restrict__ cnt,
+                          float *__restrict__ out_d, int32_t *__restrict__ out_p, int cap) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const float *x = X + s * n;
+        const float *qq = Q + (int64_t)q * n;
+        float a = 0.0f;
+        for (int j = 0; j < n; ++j) {
+            const float d = qq[j] - x[j];
+            a = fmaf(d, d, a);
+        }
+        if (a <= T) {
+            const int slot = atomicAdd(cnt, 1);
+            if (pass == 1 && slot < cap) {
+                out_d[slot] = a;
+                out_p[slot] = (int32_t)s;
+            }
+        }
+    }
+}
+
+__global__ void k_fill_u32(uint32_t *p, int64_t n, uint32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_debug_lbsax(const float *__restrict__ tab, const uint8_t *__restrict__ sax,
+                              int64_t N, int nq, float *__restrict__ out) {
+    for (int q = blockIdx.y; q < nq; q += gridDim.y)
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const float *tg = tab + (int64_t)q * kWord * kAlpha;
+        float lbs = 0.0f;
+        for (int i = 0; i < kWord; ++i) lbs += tg[i * kAlpha + sax[s * kWord + i]];
+        // the scan prunes when lbs > U(1 + 2^-18): the certified value is
+        // lbs / (1 + 2^-18) rounded down
+        out[(int64_t)q * N + s] = __fdiv_rd(lbs, 1.0f + 0x1p-18f);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+float rho_for(int n) {
+    const double u = std::ldexp(1.0, -24);
+    const double m = (double)(n + 2) * u;
+    const double g = m / (1.0 - m);
+    return (float)(g * 1.0001 + std::ldexp(1.0, -40));
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    HK_CHECK_CUDA(cudaGetDevice(&dev));
+    HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms;
+}
+
+struct ScanConfig {
+    int G;
+    int p2;
+    int cap;
+    size_t smem;
+};
+
+size_t scan_smem(int G, int n, int p2, bool sax) {
+    return (size_t)G * n * 4 + (sax ? (size_t)G * kWord * kAlpha * 4 : 0) + (size_t)G * kBT * 8 +
+           (size_t)G * p2 * 8;
+}
+
+ScanConfig choose_scan(int n, int k, bool sax, int want_G) {
+    ScanConfig c;
+    c.cap = ((k + kSlack + 31) / 32) * 32;
+    c.p2 = 32;
+    while (c.p2 < c.cap + kBT) c.p2 <<= 1;
+    const size_t limit = 200 * 1024;
+    int G = want_G > 0 ? std::min(want_G, kMaxG) : kMaxG;
+    while (G > 1 && scan_smem(G, n, c.p2, sax) > limit) G >>= 1;
+    if (G != 1 && G != 2 && G != 4 && G != 8) G = G >= 8 ? 8 : G >= 4 ? 4 : G >= 2 ? 2 : 1;
+    c.G = G;
+    c.smem = scan_smem(G, n, c.p2, sax);
+    if (c.smem > limit) fail(HK_EINVAL, "k=%d with n=%d needs %zu bytes of shared memory", k, n, c.smem);
+    return c;
+}
+
+template <int G>
+void launch_scan_g(const ScanArgs &a, size_t smem, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        HK_CHECK_CUDA(cudaFuncSetAttribute(k_scan<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           200 * 1024));
+        configured = true;
+    }
+    int per_sm = 0;
+    HK_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<G>, kBT, smem));
+    if (per_sm < 1) per_sm = 1;
+    k_scan<G><<<(unsigned)(sm_count() * per_sm), kBT, smem, s>>>(a);
+    HK_CHECK_LAUNCH();
+}
+
+void launch_scan(const ScanArgs &a, const ScanConfig &c, cudaStream_t s) {
+    switch (c.G) {
+        case 8: launch_scan_g<8>(a, c.smem, s); break;
+        case 4: launch_scan_g<4>(a, c.smem, s); break;
+        case 2: launch_scan_g<2>(a, c.smem, s); break;
+        default: launch_scan_g<1>(a, c.smem, s); break;
+    }
+}
+
+// Build leaf-major lists for mask value v and run the scan over them.
+void scan_phase(Workspace &ws, const LeafView &v, ScanArgs a, const ScanConfig &c, uint8_t val,
+                int nq, cudaStream_t s) {
+    const int64_t L = v.L;
+    k_leaf_count<<<(unsigned)L, 256, 0, s>>>(ws.mask.p, nq, val, v.leaf_off, c.G, a.S_T,
+                                            ws.leaf_qcnt.p, ws.leaf_items.p);
+    HK_CHECK_LAUNCH();
+    exclusive_scan_i32(ws.leaf_qcnt.p, ws.leaf_qoff.p, L, s, ws.scan_tmp32);
+    exclusive_scan_i64(ws.leaf_items.p, ws.item_off.p, L, s, ws.scan_tmp64);
+    k_leaf_fill<<<(unsigned)L, 256, 0, s>>>(ws.mask.p, nq, val, ws.leaf_qoff.p, ws.leaf_q.p);
+    HK_CHECK_LAUNCH();
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p, 0, sizeof(int32_t), s));
+    a.leaf_qoff = ws.leaf_qoff.p;
+    a.leaf_q = ws.leaf_q.p;
+    a.item_off = ws.item_off.p;
+    a.work_ctr = ws.counters.p;
+    launch_scan(a, c, s);
+}
+
+struct Prepared {
+    int pool_C;
+    ScanConfig cfg;
+};
+
+void reserve_common(Workspace &ws, int nq, int64_t L, int k, int pool_C, cudaStream_t s) {
+    ws.U.reserve(nq, s);
+    ws.qmode.reserve(nq, s);
+    ws.qcand.reserve(nq, s);
+    ws.mask.reserve((size_t)L * nq, s);
+    ws.leaf_qcnt.reserve(L, s);
+    ws.leaf_qoff.reserve(L + 1, s);
+    ws.leaf_q.reserve((size_t)L * nq, s);
+    ws.leaf_items.reserve(L, s);
+    ws.item_off.reserve(L + 1, s);
+    ws.counters.reserve(4, s);
+    ws.pool_d.reserve((size_t)nq * pool_C, s);
+    ws.pool_p.reserve((size_t)nq * pool_C, s);
+    ws.pool_cnt.reserve(nq, s);
+    ws.qflag.reserve(nq, s);
+    ws.rs_d.reserve((size_t)nq * pool_C, s);
+    ws.stats.reserve(kStatSlots, s);
+    ws.out_ids.reserve((size_t)nq * k, s);
+    ws.out_dist.reserve((size_t)nq * k, s);
+}
+
+void copy_out(const Workspace &ws, int nq, int k, int64_t *ids, float *dist, cudaStream_t s) {
+    const cudaMemcpyKind ki = is_device_ptr(ids) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const cudaMemcpyKind kd = is_device_ptr(dist) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    HK_CHECK_CUDA(cudaMemcpyAsync(ids, ws.out_ids.p, (size_t)nq * k * sizeof(int64_t), ki, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(dist, ws.out_dist.p, (size_t)nq * k * sizeof(float), kd, s));
+}
+
+// Final step plus the exhaustive fallback for overflowed queries.
+void finish(Workspace &ws, const LeafView &v, const float *Qd, int nq, int k, int pool_C, float rho,
+            cudaStream_t s) {
+    k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+    HK_CHECK_LAUNCH();
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p + 1, 0, sizeof(int32_t), s));
+    k_final<<<nq, 256, 0, s>>>(Qd, v.X, v.n, v.perm, ws.pool_d.p, ws.pool_p.p, ws.pool_cnt.p, pool_C,
+                               ws.U.p, ws.qflag.p, k, rho, ws.rs_d.p, ws.out_ids.p, ws.out_dist.p,
+                               (long long *)ws.stats.p, ws.counters.p + 1, nullptr);
+    HK_CHECK_LAUNCH();
+    std::vector<int32_t> flags(nq);
+    std::vector<uint32_t> U(nq);
+    int32_t err = 0;
+    HK_CHECK_CUDA(cudaMemcpyAsync(flags.data(), ws.qflag.p, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(U.data(), ws.U.p, nq * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(&err, ws.counters.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (err) fail(HK_EINTERNAL, "a query had fewer than k candidates after the scan");
+    const int sms = sm_count();
+    int64_t nfb = 0;
+    for (int q = 0; q < nq; ++q) {
+        if (!(flags[q] & 1)) continue;
+        ++nfb;
+        float T;
+        {
+            float u;
+            std::memcpy(&u, &U[q], 4);
+            T = std::nextafter(u * (1.0f + rho), INFINITY);
+        }
+        DevBuf<int32_t> cnt;
+        cnt.alloc(2, s);
+        HK_CHECK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), s));
+        k_collect<<<sms * 8, 256, 0, s>>>(Qd, q, v.X, v.n, v.N, T, 0, cnt.p, nullptr, nullptr, 0);
+        HK_CHECK_LAUNCH();
+        int32_t c = 0;
+        HK_CHECK_CUDA(cudaMemcpyAsync(&c, cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (c < k) fail(HK_EINTERNAL, "fallback for query %d found %d < k candidates", q, c);
+        DevBuf<float> fd;
+        DevBuf<int32_t> fp;
+        DevBuf<double> fr;
+        DevBuf<int32_t> qsel;
+        fd.alloc(c, s);
+        fp.alloc(c, s);
+        fr.alloc(c, s);
+        qsel.alloc(1, s);
+        HK_CHECK_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t), s));
+        k_collect<<<sms * 8, 256, 0, s>>>(Qd, q, v.X, v.n, v.N, T, 1, cnt.p, fd.p, fp.p, c);
+        HK_CHECK_LAUNCH();
+        HK_CHECK_CUDA(cudaMemcpyAsync(qsel.p, &q, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        k_final<<<1, 256, 0, s>>>(Qd, v.X, v.n, v.perm, fd.p, fp.p, cnt.p, c, ws.U.p, nullptr, k, rho,
+                                  fr.p, ws.out_ids.p, ws.out_dist.p, (long long *)ws.stats.p,
+                                  ws.counters.p + 1, qsel.p);
+        HK_CHECK_LAUNCH();
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    if (nfb) {
+        long long add = nfb;
+        // host-side counter update
+        std::vector<long long> st(kStatSlots);
+        HK_CHECK_CUDA(cudaMemcpyAsync(st.data(), ws.stats.p, kStatSlots * sizeof(long long),
+                                      cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        st[ST_FALLBACK] += add;
+        HK_CHECK_CUDA(cudaMemcpyAsync(ws.stats.p, st.data(), kStatSlots * sizeof(long long),
+                                      cudaMemcpyHostToDevice, s));
+    }
+}
+
+void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s) {
+    if (!stats) return;
+    long long st[kStatSlots];
+    HK_CHECK_CUDA(cudaMemcpyAsync(st, ws.stats.p, sizeof(st), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    std::memset(stats, 0, sizeof(*stats));
+    stats->queries = st[ST_QUERIES];
+    stats->leaves_total = st[ST_LEAVES_TOTAL];
+    stats->leaves_approx = st[ST_LEAVES_APPROX];
+    stats->leaves_candidate = st[ST_LEAVES_CAND];
+    stats->series_candidate = st[ST_SERIES_CAND];
+    stats->series_sax_pruned = st[ST_SAX_PRUNED];
+    stats->series_abandoned = st[ST_ABANDONED];
+    stats->series_full = st[ST_FULL];
+    stats->points_computed = st[ST_POINTS];
+    stats->rescored = st[ST_RESCORED];
+    stats->fallback_queries = st[ST_FALLBACK];
+    stats->work_items = st[ST_ITEMS];
+    stats->skip_sequential = st[ST_SKIPSEQ];
+}
+
+__global__ void k_count_items_and_series(const int64_t *__restrict__ item_off, int64_t L,
+                                         const int32_t *__restrict__ qcnt,
+                                         const int64_t *__restrict__ leaf_off,
+                                         long long *__restrict__ stats, int series_slot,
+                                         int leaves_slot) {
+    long long ser = 0, lv = 0;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < L;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        ser += (long long)qcnt[f] * (leaf_off[f + 1] - leaf_off[f]);
+        lv += qcnt[f];
+    }
+    ser = warp_sum_ll(ser);
+    lv = warp_sum_ll(lv);
+    if ((threadIdx.x & 31) == 0) {
+        if (series_slot >= 0 && ser)
+            stat_add(&stats[series_slot], ser);
+        if (leaves_slot >= 0 && lv)
+            stat_add(&stats[leaves_slot], lv);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        stat_add(&stats[ST_ITEMS], item_off[L]);
+}
+
+}  // namespace
+
+void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opts &o, cudaStream_t s,
+               int64_t *out_ids, float *out_dist, hk_query_stats *stats) {
+    Workspace &ws = idx->ws;
+    const int n = idx->n;
+    const int64_t L = idx->L;
+    const float rho = rho_for(n);
+    const bool noprune = (o.flags & HK_Q_NOPRUNE) != 0;
+    const bool nosax = noprune || (o.flags & HK_Q_NOSAX) != 0;
+    const int l_max = o.l_max > 0 ? o.l_max : 1;
+    const float eapca_th = o.eapca_th >= 0 ? o.eapca_th : 0.25f;
+    ScanConfig cfg = choose_scan(n, k, !nosax, o.query_group);
+    const int S_T = o.series_tile > 0 ? o.series_tile : 2048;
+    const int pool_C = std::min(65536, std::max(2048, 32 * cfg.cap));
+
+    reserve_common(ws, nq, L, k, pool_C, s);
+    ws.qseg.reserve((size_t)nq * idx->S * 2, s);
+    if (!nosax) ws.sax_tab.reserve((size_t)nq * kWord * kAlpha, s);
+    ws.lb.reserve((size_t)nq * L, s);
+    ws.approx.reserve((size_t)nq * kAmax, s);
+
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.stats.p, 0, kStatSlots * sizeof(long long), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.pool_cnt.p, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.qflag.p, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.qcand.p, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.mask.p, 0, (size_t)L * nq, s));
+    k_fill_u32<<<64, 256, 0, s>>>(ws.U.p, nq, 0x7f800000u);
+    HK_CHECK_LAUNCH();
+    {
+        long long init[kStatSlots] = {0};
+        init[ST_QUERIES] = nq;
+        init[ST_LEAVES_TOTAL] = (long long)nq * L;
+        HK_CHECK_CUDA(cudaMemcpyAsync(ws.stats.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    }
+
+    // a1 + a2
+    k_qprep<<<nq, 256, n * sizeof(float), s>>>(Qd, n, idx->seg_ab.p, idx->S, idx->bp.p, ws.qseg.p,
+                                               nosax ? nullptr : ws.sax_tab.p);
+    HK_CHECK_LAUNCH();
+    k_lb_eapca<<<dim3((unsigned)((L + 127) / 128), std::min(nq, 65535)), 128, 0, s>>>(
+        ws.qseg.p, idx->S, idx->leaf_nseg.p, idx->leaf_seg.p, idx->seg_ab.p, idx->env.p, L, nq,
+        ws.lb.p);
+    HK_CHECK_LAUNCH();
+
+    LeafView v;
+    v.X = idx->X.p;
+    v.perm = idx->perm.p;
+    v.sax = idx->sax.p;
+    v.leaf_off = idx->leaf_off.p;
+    v.N = idx->N;
+    v.n = n;
+    v.L = L;
+
+    ScanArgs a{};
+    a.v = v;
+    a.Q = Qd;
+    a.nq = nq;
+    a.sax_tab = nosax ? nullptr : ws.sax_tab.p;
+    a.qmode = ws.qmode.p;
+    a.lb = noprune ? nullptr : ws.lb.p;
+    a.U = ws.U.p;
+    a.S_T = S_T;
+    a.k = k;
+    a.cap = cfg.cap;
+    a.p2 = cfg.p2;
+    a.rho = rho;
+    a.pool_d = ws.pool_d.p;
+    a.pool_p = ws.pool_p.p;
+    a.pool_cnt = ws.pool_cnt.p;
+    a.pool_C = pool_C;
+    a.qflag = ws.qflag.p;
+    a.stats = (long long *)ws.stats.p;
+    a.use_sax = nosax ? 0 : 1;
+
+    // a3: approximate search (no LB_SAX: these leaves are scanned whole)
+    if (!noprune) {
+        k_approx_select<<<nq, 256, 0, s>>>(ws.lb.p, L, idx->leaf_off.p, l_max, k, nq, kAmax, ws.approx.p,
+                                           ws.qcand.p, ws.mask.p);
+        HK_CHECK_LAUNCH();
+        ScanArgs aa = a;
+        aa.use_sax = 0;
+        aa.lb = nullptr;
+        scan_phase(ws, v, aa, cfg, 1, nq, s);
+        k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
+                                                   (long long *)ws.stats.p, -1, ST_LEAVES_APPROX);
+        HK_CHECK_LAUNCH();
+        k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+        HK_CHECK_LAUNCH();
+        HK_CHECK_CUDA(cudaMemsetAsync(ws.qcand.p, 0, nq * sizeof(int32_t), s));
+    }
+    // a4: candidate leaves, per-query mode
+    {
+        const int64_t pairs = L * (int64_t)nq;
+        k_mask_candidates<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(ws.lb.p, L, nq, ws.U.p,
+                                                                        noprune ? 1 : 0, ws.mask.p,
+                                                                        ws.qcand.p);
+        HK_CHECK_LAUNCH();
+        k_qmode<<<(nq + 255) / 256, 256, 0, s>>>(ws.qcand.p, L, nq, eapca_th, nosax ? 1 : 0,
+                                                 (o.flags & HK_Q_NOTHRESH) ? 1 : 0, ws.qmode.p,
+                                                 (long long *)ws.stats.p);
+        HK_CHECK_LAUNCH();
+    }
+    // a5-a7: scan of the candidate leaves
+    scan_phase(ws, v, a, cfg, 2, nq, s);
+    k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
+                                               (long long *)ws.stats.p, ST_SERIES_CAND, -1);
+    HK_CHECK_LAUNCH();
+    // a8: boundary rescore and answer
+    finish(ws, v, Qd, nq, k, pool_C, rho, s);
+    copy_out(ws, nq, k, out_ids, out_dist, s);
+    copy_stats(ws, stats, s);
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+void run_scan(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k, cudaStream_t s,
+              int64_t *out_ids, float *out_dist) {
+    Workspace ws;
+    const float rho = rho_for(n);
+    ScanConfig cfg = choose_scan(n, k, false, 0);
+    const int S_T = 2048;
+    const int pool_C = std::min(65536, std::max(2048, 32 * cfg.cap));
+    reserve_common(ws, nq, 1, k, pool_C, s);
+    DevBuf<int64_t> leaf_off;
+    leaf_off.alloc(2, s);
+    const int64_t lo[2] = {0, N};
+    HK_CHECK_CUDA(cudaMemcpyAsync(leaf_off.p, lo, sizeof(lo), cudaMemcpyHostToDevice, s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.stats.p, 0, kStatSlots * sizeof(long long), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.pool_cnt.p, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.qflag.p, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.mask.p, 2, (size_t)nq, s));
+    k_fill_u32<<<64, 256, 0, s>>>(ws.U.p, nq, 0x7f800000u);
+    HK_CHECK_LAUNCH();
+    LeafView v;
+    v.X = Xd;
+    v.perm = nullptr;
+    v.sax = nullptr;
+    v.leaf_off = leaf_off.p;
+    v.N = N;
+    v.n = n;
+    v.L = 1;
+    ScanArgs a{};
+    a.v = v;
+    a.Q = Qd;
+    a.nq = nq;
+    a.U = ws.U.p;
+    a.S_T = S_T;
+    a.k = k;
+    a.cap = cfg.cap;
+    a.p2 = cfg.p2;
+    a.rho = rho;
+    a.pool_d = ws.pool_d.p;
+    a.pool_p = ws.pool_p.p;
+    a.pool_cnt = ws.pool_cnt.p;
+    a.pool_C = pool_C;
+    a.qflag = ws.qflag.p;
+    a.stats = (long long *)ws.stats.p;
+    a.use_sax = 0;
+    scan_phase(ws, v, a, cfg, 2, nq, s);
+    finish(ws, v, Qd, nq, k, pool_C, rho, s);
+    copy_out(ws, nq, k, out_ids, out_dist, s);
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+void debug_lb_eapca(hk_index *idx, const float *Qd, int nq, double *out_host) {
+    cudaStream_t s = idx->stream;
+    Workspace &ws = idx->ws;
+    ws.qseg.reserve((size_t)nq * idx->S * 2, s);
+    ws.lb.reserve((size_t)nq * idx->L, s);
+    k_qprep<<<nq, 256, idx->n * sizeof(float), s>>>(Qd, idx->n, idx->seg_ab.p, idx->S, idx->bp.p,
+                                                    ws.qseg.p, nullptr);
+    HK_CHECK_LAUNCH();
+    k_lb_eapca<<<dim3((unsigned)((idx->L + 127) / 128), std::min(nq, 65535)), 128, 0, s>>>(
+        ws.qseg.p, idx->S, idx->leaf_nseg.p, idx->leaf_seg.p, idx->seg_ab.p, idx->env.p, idx->L, nq,
+        ws.lb.p);
+    HK_CHECK_LAUNCH();
+    HK_CHECK_CUDA(cudaMemcpyAsync(out_host, ws.lb.p, (size_t)nq * idx->L * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+void debug_lb_sax(hk_index *idx, const float *Qd, int nq, float *out_host) {
+    cudaStream_t s = idx->stream;
+    Workspace &ws = idx->ws;
+    ws.sax_tab.reserve((size_t)nq * kWord * kAlpha, s);
+    k_qprep<<<nq, 256, idx->n * sizeof(float), s>>>(Qd, idx->n, idx->seg_ab.p, idx->S, idx->bp.p,
+                                                    nullptr, ws.sax_tab.p);
+    HK_CHECK_LAUNCH();
+    DevBuf<float> out;
+    out.alloc((size_t)nq * idx->N, s);
+    k_debug_lbsax<<<dim3(256, std::min(nq, 65535)), 256, 0, s>>>(ws.sax_tab.p, idx->sax.p, idx->N, nq, out.p);
+    HK_CHECK_LAUNCH();
+    HK_CHECK_CUDA(cudaMemcpyAsync(out_host, out.p, (size_t)nq * idx->N * sizeof(float),
+                                  cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace hk
