@@ -1,0 +1,341 @@
+"""Benchmark: exact k-NN queries/s on one GB300 (or N replicas).
+
+Workload (default "large"): 100,000,000 random-walk series x 256 float32
+(z-normalised, seed 0) indexed with leaf capacity 100,000; 10,000 hard queries
+(a dataset series plus N(0, sigma^2) noise, sigma alternating 0.5 / 1.0,
+re-z-normalised, seed 1); k = 10.  A step answers one batch of queries (1,000
+by default) through the whole path: query preparation, LB_EAPCA, the
+approximate search, leaf pruning, LB_SAX, the early-abandoning distance scan,
+top-k, and the binary64 boundary rescore.  Consecutive steps take consecutive
+batches of the 10,000 queries.
+
+Prints one JSON line.  `--impl reference` times the oracle (plain binary64
+brute force on the host cores) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: N, n, leaf capacity, total queries, noise sigmas, k, queries per step
+    "large": dict(N=100_000_000, n=256, tau=100_000, nq=10_000, sigmas=[0.5, 1.0], k=10, batch=1000,
+                  desc="100M random walks x 256, leaf 100K, 10K hard queries (sigma 0.5/1.0), k=10"),
+    "mid": dict(N=10_000_000, n=256, tau=10_000, nq=100, sigmas=[0.01, 0.1, 0.5, 1.0], k=10, batch=100,
+                desc="10M random walks x 256, leaf 10K, 100 queries (sigma 0.01/0.1/0.5/1.0), k=10"),
+    "small": dict(N=100_000, n=256, tau=1_000, nq=10, sigmas=[0.1], k=1, batch=10,
+                  desc="100K random walks x 256, leaf 1K, 10 queries (sigma 0.1), k=1"),
+}
+
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2070.0),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(smax) if smax else None, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(X_sample, Q, N_full, budget_s=10.0, chunk=250_000):
+    """Oracle queries/s over a collection of N_full series, extrapolated from
+    the time it takes to scan a sample of rows for len(Q) queries."""
+    import oracle
+    s = oracle.KnnStream(Q, 10)
+    done = 0
+    t0 = time.perf_counter()
+    while done < X_sample.shape[0]:
+        blk = X_sample[done:done + chunk]
+        s.update(blk, done)
+        done += blk.shape[0]
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    qps = Q.shape[0] / (dt * (N_full / done))
+    return qps, dt, done, s.nthreads
+
+
+def run_reference(args, wl):
+    """The reference arm: the oracle as it stands, on the host cores."""
+    import numpy as np
+    import torch
+    from paper_2212_13297_gb300 import workload
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    rows = 1_000_000
+    X = workload.random_walk(rows, wl["n"], seed=0, device="cpu").numpy()
+    cores = len(os.sched_getaffinity(0))
+    nqb = max(1, min(16, cores))
+    Qt, _ = workload.queries(torch.from_numpy(X), nqb * (args.steps + args.warmup), wl["sigmas"], seed=1)
+    Q = Qt.numpy()
+    import oracle
+    oracle._lib()
+    times = []
+    for i in range(args.warmup + args.steps):
+        q = Q[i * nqb:(i + 1) * nqb]
+        t0 = time.perf_counter()
+        s = oracle.KnnStream(q, wl["k"], nthreads=cores)
+        s.update(X[:250_000], 0)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    # one step = nqb queries over 250K rows; scale to the full collection
+    scale = wl["N"] / 250_000
+    per_step = statistics.mean(times) * scale
+    value = nqb / per_step
+    line = dict(impl="reference", metric="exact %d-NN queries/s" % wl["k"], value=value,
+                unit="queries/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                ms_per_step=per_step * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=wl["desc"], N=wl["N"], n=wl["n"], k=wl["k"]),
+                cpu_baseline=dict(value=value, unit="queries/s", cores=cores, kind="oracle",
+                                  sample="%d queries x 250,000 of the series per step, "
+                                         "time scaled by %.0fx to %d series" % (nqb, scale, wl["N"])),
+                e2e=dict(value=value, unit="queries/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="queries per step (0 = workload default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--query-group", type=int, default=0)
+    ap.add_argument("--series-tile", type=int, default=0)
+    ap.add_argument("--l-max", type=int, default=0)
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.batch:
+        wl["batch"] = args.batch
+
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2212_13297_gb300 import binding, workload
+    import __graft_entry__
+    __graft_entry__.build()
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+
+    N, n, k, B = wl["N"], wl["n"], wl["k"], wl["batch"]
+    t0 = time.perf_counter()
+    X = workload.random_walk(N, n, seed=0, device="cuda")
+    Q_all, _ = workload.queries(X, wl["nq"], wl["sigmas"], seed=1)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    sample = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sample = X[:min(N, 4_000_000)].cpu().numpy()
+    t0 = time.perf_counter()
+    idx = binding.Index(X, wl["tau"])
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    info = idx.info()
+    del X
+    torch.cuda.empty_cache()
+
+    nb = max(1, wl["nq"] // B)
+    batches = [Q_all[(i % nb) * B:(i % nb + 1) * B].contiguous() for i in range(args.warmup + args.steps)]
+    ids = torch.empty((B, k), dtype=torch.int64, device="cuda")
+    dist_out = torch.empty((B, k), dtype=torch.float32, device="cuda")
+    qkw = dict(l_max=args.l_max, query_group=args.query_group, series_tile=args.series_tile)
+
+    for i in range(args.warmup):
+        idx.query(batches[i], k, flags=binding.HK_Q_TIMING, out=(ids, dist_out), **qkw)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev_index)
+    sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    step_lat, agg = [], {}
+    for i in range(args.steps):
+        ts = time.perf_counter()
+        _, _, st = idx.query(batches[args.warmup + i], k, flags=binding.HK_Q_TIMING,
+                             out=(ids, dist_out), **qkw)
+        step_lat.append(time.perf_counter() - ts)
+        for key, v in st.items():
+            agg[key] = agg.get(key, 0) + v
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_dev], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = ws * B * args.steps / t_dev
+
+    # end to end through the C ABI with host buffers (pinned queries in,
+    # host results out; the copies are inside each call)
+    e2e = None
+    if not args.no_e2e:
+        hq = [batches[args.warmup + i].cpu().pin_memory() for i in range(args.steps)]
+        hid = np.empty((B, k), np.int64)
+        hdi = np.empty((B, k), np.float32)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        te = time.perf_counter()
+        for i in range(args.steps):
+            idx.query(hq[i], k, out=(hid, hdi), **qkw)
+        t_e2e = time.perf_counter() - te
+        if ws > 1:
+            t = torch.tensor([t_e2e], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = dict(value=ws * B * args.steps / t_e2e, unit="queries/s",
+                   h2d_bytes_per_step=B * n * 4, d2h_bytes_per_step=B * k * 12)
+
+    if rank != 0:
+        return
+    pk = peaks()
+    scan_s = agg["scan_ns"] / 1e9
+    flops = 3.0 * agg["points_computed"]
+    alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    alu_ach = flops / scan_s / 1e12 if scan_s else None
+    hbm_ach = agg["scan_bytes"] / scan_s / 1e9 if scan_s else None
+    alu_frac = alu_ach / alu_peak if alu_ach else 0
+    hbm_frac = hbm_ach / pk["hbm_gbs"] if hbm_ach else 0
+    if alu_frac >= hbm_frac:
+        roof = dict(bound="alu", achieved=alu_ach, peak=alu_peak, unit="TFLOP/s", frac=alu_frac,
+                    traffic=None, kernel="k_scan",
+                    peak_note="FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz; 3 flops per "
+                              "(q-x)^2 point" % pk["sm_max_mhz"],
+                    hbm_side=dict(achieved=hbm_ach, peak=pk["hbm_gbs"], unit="GB/s", frac=hbm_frac,
+                                  peak_source=pk["source"]))
+    else:
+        roof = dict(bound="hbm", achieved=hbm_ach, peak=pk["hbm_gbs"], unit="GB/s", frac=hbm_frac,
+                    traffic=None, kernel="k_scan", peak_source=pk["source"],
+                    alu_side=dict(achieved=alu_ach, peak=alu_peak, unit="TFLOP/s", frac=alu_frac))
+    roof["scan_share_of_step"] = scan_s / t_dev if t_dev else None
+
+    cpu = None
+    if sample is not None:
+        cores = len(os.sched_getaffinity(0))
+        nqb = max(1, min(16, cores))
+        qps, dt, rows, thr = cpu_oracle_rate(sample, Q_all[:nqb].cpu().numpy(), N)
+        cpu = dict(value=qps, unit="queries/s", cores=thr, kind="oracle",
+                   sample="%d queries x first %d series (%.1f s of CPU), time scaled to %d series"
+                          % (nqb, rows, dt, N))
+
+    lat = sorted(step_lat)
+    line = dict(
+        metric="exact %d-NN queries/s (%s)" % (k, "%dM x %d" % (N // 1_000_000, n) if N >= 1_000_000 else "%d x %d" % (N, n)),
+        value=value, unit="queries/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+        ms_per_step=t_dev / args.steps * 1e3, higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload=wl["desc"], N=N, n=n, leaf_capacity=wl["tau"], k=k,
+                    queries_per_step=B, queries_total=wl["nq"], parallelism="replicas" if ws > 1 else "1 GPU",
+                    l2="inputs larger than L2 (%.0f GB collection)" % (N * n * 4 / 1e9)),
+        latency_ms=dict(kind="batch completion (closed loop, %d queries per batch)" % B,
+                        p50=lat[len(lat) // 2] * 1e3, p99=lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3),
+        clocks=clocks, e2e=e2e, gpu_launches=agg["kernel_launches"], roofline=roof,
+        cpu_baseline=cpu,
+        pruning=dict(leaves_candidate_frac=agg["leaves_candidate"] / max(1, agg["leaves_total"]),
+                     series_candidate=agg["series_candidate"], sax_pruned=agg["series_sax_pruned"],
+                     abandoned=agg["series_abandoned"], full=agg["series_full"],
+                     points=agg["points_computed"], rescored=agg["rescored"],
+                     fallback=agg["fallback_queries"], skip_sequential=agg["skip_sequential"]),
+        index=dict(build_s=t_build, gen_s=t_gen, leaves=info["leaves"], depth=info["depth"],
+                   max_segments=info["max_segments"]),
+    )
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

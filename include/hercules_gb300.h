@@ -95,6 +95,8 @@ int hk_index_info_get(const hk_index *idx, hk_index_info *out);
 #define HK_Q_NOSAX 1u      /* skip LB_SAX filtering (ablation, Sec. 4.2)      */
 #define HK_Q_NOTHRESH 2u   /* ignore EAPCA_TH / SAX_TH (ablation)             */
 #define HK_Q_NOPRUNE 4u    /* scan every series (parallel-scan baseline)      */
+#define HK_Q_TIMING 8u     /* time the scan kernels with CUDA events on the
+                              call's stream (hk_query_stats.scan_ns)          */
 
 typedef struct {
     int32_t l_max;        /* leaves visited by the approximate search per query
@@ -118,9 +120,14 @@ typedef struct {
     int64_t points_computed;      /* (q - x)^2 terms evaluated                   */
     int64_t rescored;             /* binary64 boundary rescores                  */
     int64_t fallback_queries;     /* queries finished by the exhaustive collect  */
+    int64_t retried_queries;      /* queries run again from their final bound
+                                     after a candidate list or pool overflowed  */
     int64_t work_items;           /* scan work items launched                    */
     int64_t skip_sequential;      /* queries scanned without LB_SAX (EAPCA_TH)   */
-    int64_t reserved[3];
+    int64_t scan_ns;              /* scan kernel time (HK_Q_TIMING), ns          */
+    int64_t kernel_launches;      /* kernels this call launched                  */
+    int64_t scan_bytes;           /* series bytes the scan read: 64 B per 16-point
+                                     chunk loaded + 16 B per iSAX word, per item */
 } hk_query_stats;
 
 /*

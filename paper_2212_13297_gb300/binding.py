@@ -28,6 +28,7 @@ HK_BUILD_BF16 = 2
 HK_Q_NOSAX = 1
 HK_Q_NOTHRESH = 2
 HK_Q_NOPRUNE = 4
+HK_Q_TIMING = 8
 
 
 class hk_build_opts(ctypes.Structure):
@@ -45,11 +46,11 @@ class hk_query_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "queries", "leaves_total", "leaves_approx", "leaves_candidate", "series_candidate",
         "series_sax_pruned", "series_abandoned", "series_full", "points_computed", "rescored",
-        "fallback_queries", "work_items", "skip_sequential", "r0", "r1", "r2")]
+        "fallback_queries", "retried_queries", "work_items", "skip_sequential", "scan_ns", "kernel_launches",
+        "scan_bytes")]
 
     def as_dict(self):
-        return {f[0]: getattr(self, f[0]) for f in self._fields_ if not f[0].startswith("r") or
-                f[0] == "rescored"}
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
 class hk_index_info(ctypes.Structure):

@@ -7,6 +7,8 @@
 
 namespace hk {
 
+thread_local long long g_launches = 0;
+
 namespace {
 thread_local std::string g_last_error;
 }

@@ -35,7 +35,12 @@ void clear_last_error();
                        __FILE__, __LINE__);                                    \
     } while (0)
 
-#define HK_CHECK_LAUNCH() HK_CHECK_CUDA(cudaGetLastError())
+extern thread_local long long g_launches;   // kernels launched by this thread
+#define HK_CHECK_LAUNCH()                       \
+    do {                                        \
+        HK_CHECK_CUDA(cudaGetLastError());      \
+        ++::hk::g_launches;                     \
+    } while (0)
 
 // ---------------------------------------------------------------- device memory
 // Owning device buffer.  cudaMalloc/cudaFree: cudaFree waits for the device,
@@ -90,7 +95,7 @@ void exclusive_scan_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t
 struct Workspace {
     DevBuf<float> Q;            // nq * n
     DevBuf<double> qseg;        // nq * S * 2  (mu, sd) per distinct segment
-    DevBuf<float> sax_tab;      // nq * 16 * 256 LB_SAX table (rounded down)
+    DevBuf<uint16_t> sax_tab;   // nq * 16 * 256 LB_SAX table (float16, rounded down)
     DevBuf<double> lb;          // nq * L
     DevBuf<uint32_t> U;         // nq   bound on the k-th distance (float bits)
     DevBuf<uint8_t> qmode;      // nq   bit0: LB_SAX filter on
@@ -113,6 +118,8 @@ struct Workspace {
     DevBuf<int64_t> out_ids;    // nq * k
     DevBuf<float> out_dist;     // nq * k
     DevBuf<int32_t> approx;     // nq * A
+    DevBuf<uint32_t> Uinit;     // retry pass: starting bounds
+    DevBuf<int32_t> sel;        // retry pass: rows of the batch it answers
 };
 
 // Device view of a collection laid out by leaves (an index, or a plain
@@ -156,6 +163,7 @@ struct hk_index {
     std::vector<int32_t> h_seg_end;   // L*kMaxSeg
 
     hk::Workspace ws;
+    hk::Workspace ws_retry;
 };
 
 namespace hk {

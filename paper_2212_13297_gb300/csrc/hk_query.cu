@@ -36,6 +36,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "hk_device.cuh"
 #include "hk_internal.cuh"
 
@@ -45,20 +47,20 @@ namespace {
 constexpr int kBT = 256;       // scan CTA threads = series per chunk
 constexpr int kSlack = 32;     // room for near-ties beyond k in an item list
 constexpr int kMaxG = 8;
-constexpr int kStatSlots = 16;
+constexpr int kStatSlots = 24;
 constexpr int kAmax = 256;     // most leaves the approximate step visits
 
 enum StatIdx {
     ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_APPROX, ST_LEAVES_CAND, ST_SERIES_CAND,
     ST_SAX_PRUNED, ST_ABANDONED, ST_FULL, ST_POINTS, ST_RESCORED, ST_FALLBACK,
-    ST_ITEMS, ST_SKIPSEQ
+    ST_ITEMS, ST_SKIPSEQ, ST_SCAN_NS, ST_LAUNCHES, ST_SCAN_BYTES, ST_RETRIED
 };
 
 struct ScanArgs {
     LeafView v;
     const float *Q;
     int nq;
-    const float *sax_tab;      // nq*16*256 or nullptr
+    const __half *sax_tab;     // nq*16*256 or nullptr
     const uint8_t *qmode;      // nq (bit0: LB_SAX on) or nullptr
     const double *lb;          // nq*L or nullptr
     uint32_t *U;               // nq float bits
@@ -85,10 +87,11 @@ __device__ __forceinline__ float upper_f(float d, float rho) { return __fmul_ru(
 // --------------------------------------------------------------------------
 // a1: query preparation.  Per query: mean and std of every distinct leaf
 // segment (binary64, the build's exact definition), PAA over 16 segments, and
-// the LB_SAX table T[i][s] = (n/16) dist(PAA_i, cell s)^2 rounded down.
+// the LB_SAX table T[i][s] = (n/16) dist(PAA_i, cell s)^2 rounded down to
+// float16 (8 KB per query, so a scan CTA holds the tables of its queries).
 __global__ void k_qprep(const float *__restrict__ Q, int n, const int32_t *__restrict__ seg_ab,
                         int64_t S, const float *__restrict__ bp, double *__restrict__ qseg,
-                        float *__restrict__ tab) {
+                        __half *__restrict__ tab) {
     extern __shared__ float qs[];
     __shared__ double paa[kWord];
     __shared__ float bps[255];
@@ -115,7 +118,9 @@ __global__ void k_qprep(const float *__restrict__ Q, int n, const int32_t *__res
             const double lo = sym == 0 ? -INFINITY : (double)bps[sym - 1];
             const double hi = sym == kAlpha - 1 ? INFINITY : (double)bps[sym];
             const double d = dist_to_range64(paa[i], lo, hi);
-            tab[(int64_t)q * kWord * kAlpha + t] = __double2float_rd(__dmul_rn(w, __dmul_rn(d, d)));
+            // rounded down twice (binary64 -> float32 -> float16): a lower value
+            tab[(int64_t)q * kWord * kAlpha + t] =
+                __float2half_rd(__double2float_rd(__dmul_rn(w, __dmul_rn(d, d))));
         }
     }
 }
@@ -298,8 +303,8 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.v.n;
     float *q_s = reinterpret_cast<float *>(smem_raw);                 // G*n
-    float *tab_s = q_s + G * n;                                       // G*4096 if use_sax
-    float *stage_d = tab_s + (A.use_sax ? G * kWord * kAlpha : 0);    // G*kBT
+    __half *tab_s = reinterpret_cast<__half *>(q_s + G * n);          // G*4096 if use_sax
+    float *stage_d = reinterpret_cast<float *>(tab_s + (A.use_sax ? G * kWord * kAlpha : 0));
     int32_t *stage_p = reinterpret_cast<int32_t *>(stage_d + G * kBT);
     float *list_d = reinterpret_cast<float *>(stage_p + G * kBT);     // G*p2
     int32_t *list_p = reinterpret_cast<int32_t *>(list_d + G * A.p2);
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t total = A.item_off[A.v.L];
     const float rho = A.rho;
-    long long my_sax = 0, my_ab = 0, my_full = 0, my_pts = 0;
+    long long my_sax = 0, my_ab = 0, my_full = 0, my_pts = 0, my_bytes = 0;
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(A.work_ctr, 1);
@@ -373,9 +378,9 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
             float4 *dst = reinterpret_cast<float4 *>(q_s + g * n);
             for (int j = tid; j < (n >> 2); j += kBT) dst[j] = src[j];
             if (sax_mask >> g & 1) {
-                const float4 *ts = reinterpret_cast<const float4 *>(A.sax_tab + (int64_t)s_qid[g] * kWord * kAlpha);
-                float4 *td = reinterpret_cast<float4 *>(tab_s + g * kWord * kAlpha);
-                for (int j = tid; j < kWord * kAlpha / 4; j += kBT) td[j] = ts[j];
+                const uint4 *ts = reinterpret_cast<const uint4 *>(A.sax_tab + (int64_t)s_qid[g] * kWord * kAlpha);
+                uint4 *td = reinterpret_cast<uint4 *>(tab_s + g * kWord * kAlpha);
+                for (int j = tid; j < kWord * kAlpha / 8; j += kBT) td[j] = ts[j];
             }
         }
         __syncthreads();
@@ -394,11 +399,11 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         if (!(sax_mask >> g & 1)) continue;
-                        const float *tg = tab_s + g * kWord * kAlpha;
+                        const __half *tg = tab_s + g * kWord * kAlpha;
                         float lbs = 0.0f;
 #pragma unroll
                         for (int i = 0; i < kWord; ++i)
-                            lbs += tg[i * kAlpha + ((wv[i >> 2] >> ((i & 3) * 8)) & 0xff)];
+                            lbs += __half2float(tg[i * kAlpha + ((wv[i >> 2] >> ((i & 3) * 8)) & 0xff)]);
                         if (lbs > s_Tsax[g]) {
                             act &= ~(1u << g);
                             ++my_sax;
@@ -408,12 +413,19 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
                 float acc[G];
 #pragma unroll
                 for (int g = 0; g < G; ++g) acc[g] = 0.0f;
+                if (sax_mask) my_bytes += kWord;
                 const float4 *xr = reinterpret_cast<const float4 *>(A.v.X + s * n);
+                float4 x0 = __ldg(xr + 0), x1 = __ldg(xr + 1), x2 = __ldg(xr + 2), x3 = __ldg(xr + 3);
                 for (int j = 0; j < n && act; j += 16) {
-                    const float4 x0 = __ldg(xr + (j >> 2) + 0);
-                    const float4 x1 = __ldg(xr + (j >> 2) + 1);
-                    const float4 x2 = __ldg(xr + (j >> 2) + 2);
-                    const float4 x3 = __ldg(xr + (j >> 2) + 3);
+                    my_bytes += 64;
+                    // prefetch the next 16 points while these are consumed
+                    float4 y0 = x0, y1 = x1, y2 = x2, y3 = x3;
+                    if (j + 16 < n) {
+                        y0 = __ldg(xr + (j >> 2) + 4);
+                        y1 = __ldg(xr + (j >> 2) + 5);
+                        y2 = __ldg(xr + (j >> 2) + 6);
+                        y3 = __ldg(xr + (j >> 2) + 7);
+                    }
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         if (!(act >> g & 1)) continue;
@@ -443,6 +455,7 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
                             ++my_ab;
                         }
                     }
+                    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
                 }
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
@@ -548,7 +561,9 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
     my_ab = warp_sum_ll(my_ab);
     my_full = warp_sum_ll(my_full);
     my_pts = warp_sum_ll(my_pts);
+    my_bytes = warp_sum_ll(my_bytes);
     if (lane == 0) {
+        stat_add(&A.stats[ST_SCAN_BYTES], my_bytes);
         stat_add(&A.stats[ST_SAX_PRUNED], my_sax);
         stat_add(&A.stats[ST_ABANDONED], my_ab);
         stat_add(&A.stats[ST_FULL], my_full);
@@ -654,21 +669,25 @@ __global__ void k_final(const float *__restrict__ Q, const float *__restrict__ X
     }
 }
 
-// Fallback: every series of the collection whose float32 distance to query q
-// is at or below T(U[q]) (pass 0 counts, pass 1 writes).
+// Last-resort fallback: every series of the collection whose float32
+// distance to query q is at or below T (pass 0 counts, pass 1 writes).  One
+// warp per series, coalesced reads; any summation order obeys the same
+// rounding bound.
 __global__ void k_collect(const float *__restrict__ Q, int q, const float *__restrict__ X, int n,
                           int64_t N, float T, int pass, int32_t *__restrict__ cnt,
                           float *__restrict__ out_d, int32_t *__restrict__ out_p, int cap) {
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N;
-         s += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float *qq = Q + (int64_t)q * n;
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < N; s += warps) {
         const float *x = X + s * n;
-        const float *qq = Q + (int64_t)q * n;
         float a = 0.0f;
-        for (int j = 0; j < n; ++j) {
+        for (int j = lane; j < n; j += 32) {
             const float d = qq[j] - x[j];
             a = fmaf(d, d, a);
         }
-        if (a <= T) {
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0 && a <= T) {
             const int slot = atomicAdd(cnt, 1);
             if (pass == 1 && slot < cap) {
                 out_d[slot] = a;
@@ -678,20 +697,44 @@ __global__ void k_collect(const float *__restrict__ Q, int q, const float *__res
     }
 }
 
+// Rows sel[i] of Q and U into compact arrays (the queries of a retry pass).
+__global__ void k_gather_queries(const float *__restrict__ Q, int n, const int32_t *__restrict__ sel,
+                                 int nsel, const uint32_t *__restrict__ U, float *__restrict__ Qo,
+                                 uint32_t *__restrict__ Uo) {
+    const int i = blockIdx.x;
+    if (i >= nsel) return;
+    const int q = sel[i];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) Qo[(int64_t)i * n + j] = Q[(int64_t)q * n + j];
+    if (threadIdx.x == 0) Uo[i] = U[q];
+}
+
+// Results of a retry pass back into the batch's rows.
+__global__ void k_scatter_results(const int64_t *__restrict__ ids, const float *__restrict__ dist,
+                                  const int32_t *__restrict__ sel, int nsel, int k,
+                                  int64_t *__restrict__ ids_o, float *__restrict__ dist_o) {
+    const int i = blockIdx.x;
+    if (i >= nsel) return;
+    const int q = sel[i];
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        ids_o[(int64_t)q * k + t] = ids[(int64_t)i * k + t];
+        dist_o[(int64_t)q * k + t] = dist[(int64_t)i * k + t];
+    }
+}
+
 __global__ void k_fill_u32(uint32_t *p, int64_t n, uint32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
 }
 
-__global__ void k_debug_lbsax(const float *__restrict__ tab, const uint8_t *__restrict__ sax,
+__global__ void k_debug_lbsax(const __half *__restrict__ tab, const uint8_t *__restrict__ sax,
                               int64_t N, int nq, float *__restrict__ out) {
     for (int q = blockIdx.y; q < nq; q += gridDim.y)
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const float *tg = tab + (int64_t)q * kWord * kAlpha;
+        const __half *tg = tab + (int64_t)q * kWord * kAlpha;
         float lbs = 0.0f;
-        for (int i = 0; i < kWord; ++i) lbs += tg[i * kAlpha + sax[s * kWord + i]];
+        for (int i = 0; i < kWord; ++i) lbs += __half2float(tg[i * kAlpha + sax[s * kWord + i]]);
         // the scan prunes when lbs > U(1 + 2^-18): the certified value is
         // lbs / (1 + 2^-18) rounded down
         out[(int64_t)q * N + s] = __fdiv_rd(lbs, 1.0f + 0x1p-18f);
@@ -721,7 +764,7 @@ struct ScanConfig {
 };
 
 size_t scan_smem(int G, int n, int p2, bool sax) {
-    return (size_t)G * n * 4 + (sax ? (size_t)G * kWord * kAlpha * 4 : 0) + (size_t)G * kBT * 8 +
+    return (size_t)G * n * 4 + (sax ? (size_t)G * kWord * kAlpha * 2 : 0) + (size_t)G * kBT * 8 +
            (size_t)G * p2 * 8;
 }
 
@@ -730,7 +773,7 @@ ScanConfig choose_scan(int n, int k, bool sax, int want_G) {
     c.cap = ((k + kSlack + 31) / 32) * 32;
     c.p2 = 32;
     while (c.p2 < c.cap + kBT) c.p2 <<= 1;
-    const size_t limit = 200 * 1024;
+    const size_t limit = 200 * 1024;   // bytes of dynamic shared memory
     int G = want_G > 0 ? std::min(want_G, kMaxG) : kMaxG;
     while (G > 1 && scan_smem(G, n, c.p2, sax) > limit) G >>= 1;
     if (G != 1 && G != 2 && G != 4 && G != 8) G = G >= 8 ? 8 : G >= 4 ? 4 : G >= 2 ? 2 : 1;
@@ -764,9 +807,35 @@ void launch_scan(const ScanArgs &a, const ScanConfig &c, cudaStream_t s) {
     }
 }
 
+// CUDA events bracketing each scan launch on its stream (HK_Q_TIMING).
+struct ScanTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    ~ScanTimer() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    void mark(cudaStream_t s) {
+        if (!on) return;
+        cudaEvent_t e;
+        HK_CHECK_CUDA(cudaEventCreate(&e));
+        ev.push_back(e);
+        HK_CHECK_CUDA(cudaEventRecord(e, s));
+    }
+    // total of (end - start) over the recorded pairs, after the stream finished
+    long long total_ns() {
+        double ms = 0.0;
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float t = 0.f;
+            HK_CHECK_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+            ms += t;
+        }
+        return (long long)(ms * 1e6);
+    }
+};
+
 // Build leaf-major lists for mask value v and run the scan over them.
 void scan_phase(Workspace &ws, const LeafView &v, ScanArgs a, const ScanConfig &c, uint8_t val,
-                int nq, cudaStream_t s) {
+                int nq, cudaStream_t s, ScanTimer *timer = nullptr) {
     const int64_t L = v.L;
     k_leaf_count<<<(unsigned)L, 256, 0, s>>>(ws.mask.p, nq, val, v.leaf_off, c.G, a.S_T,
                                             ws.leaf_qcnt.p, ws.leaf_items.p);
@@ -780,7 +849,9 @@ void scan_phase(Workspace &ws, const LeafView &v, ScanArgs a, const ScanConfig &
     a.leaf_q = ws.leaf_q.p;
     a.item_off = ws.item_off.p;
     a.work_ctr = ws.counters.p;
+    if (timer) timer->mark(s);
     launch_scan(a, c, s);
+    if (timer) timer->mark(s);
 }
 
 struct Prepared {
@@ -816,9 +887,10 @@ void copy_out(const Workspace &ws, int nq, int k, int64_t *ids, float *dist, cud
     HK_CHECK_CUDA(cudaMemcpyAsync(dist, ws.out_dist.p, (size_t)nq * k * sizeof(float), kd, s));
 }
 
-// Final step plus the exhaustive fallback for overflowed queries.
-void finish(Workspace &ws, const LeafView &v, const float *Qd, int nq, int k, int pool_C, float rho,
-            cudaStream_t s) {
+// a8: tighten U from the pool, rescore in binary64 and select.  Returns the
+// per-query flags (bit0: a list or the pool overflowed) and bounds on the host.
+void final_select(Workspace &ws, const LeafView &v, const float *Qd, int nq, int k, int pool_C,
+                  float rho, cudaStream_t s, std::vector<int32_t> &flags, std::vector<uint32_t> &U) {
     k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
     HK_CHECK_LAUNCH();
     HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p + 1, 0, sizeof(int32_t), s));
@@ -826,66 +898,67 @@ void finish(Workspace &ws, const LeafView &v, const float *Qd, int nq, int k, in
                                ws.U.p, ws.qflag.p, k, rho, ws.rs_d.p, ws.out_ids.p, ws.out_dist.p,
                                (long long *)ws.stats.p, ws.counters.p + 1, nullptr);
     HK_CHECK_LAUNCH();
-    std::vector<int32_t> flags(nq);
-    std::vector<uint32_t> U(nq);
+    flags.assign(nq, 0);
+    U.assign(nq, 0);
     int32_t err = 0;
     HK_CHECK_CUDA(cudaMemcpyAsync(flags.data(), ws.qflag.p, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HK_CHECK_CUDA(cudaMemcpyAsync(U.data(), ws.U.p, nq * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     HK_CHECK_CUDA(cudaMemcpyAsync(&err, ws.counters.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
     if (err) fail(HK_EINTERNAL, "a query had fewer than k candidates after the scan");
-    const int sms = sm_count();
-    int64_t nfb = 0;
-    for (int q = 0; q < nq; ++q) {
-        if (!(flags[q] & 1)) continue;
-        ++nfb;
-        float T;
-        {
-            float u;
-            std::memcpy(&u, &U[q], 4);
-            T = std::nextafter(u * (1.0f + rho), INFINITY);
-        }
-        DevBuf<int32_t> cnt;
-        cnt.alloc(2, s);
-        HK_CHECK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), s));
-        k_collect<<<sms * 8, 256, 0, s>>>(Qd, q, v.X, v.n, v.N, T, 0, cnt.p, nullptr, nullptr, 0);
-        HK_CHECK_LAUNCH();
-        int32_t c = 0;
-        HK_CHECK_CUDA(cudaMemcpyAsync(&c, cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        HK_CHECK_CUDA(cudaStreamSynchronize(s));
-        if (c < k) fail(HK_EINTERNAL, "fallback for query %d found %d < k candidates", q, c);
-        DevBuf<float> fd;
-        DevBuf<int32_t> fp;
-        DevBuf<double> fr;
-        DevBuf<int32_t> qsel;
-        fd.alloc(c, s);
-        fp.alloc(c, s);
-        fr.alloc(c, s);
-        qsel.alloc(1, s);
-        HK_CHECK_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t), s));
-        k_collect<<<sms * 8, 256, 0, s>>>(Qd, q, v.X, v.n, v.N, T, 1, cnt.p, fd.p, fp.p, c);
-        HK_CHECK_LAUNCH();
-        HK_CHECK_CUDA(cudaMemcpyAsync(qsel.p, &q, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        k_final<<<1, 256, 0, s>>>(Qd, v.X, v.n, v.perm, fd.p, fp.p, cnt.p, c, ws.U.p, nullptr, k, rho,
-                                  fr.p, ws.out_ids.p, ws.out_dist.p, (long long *)ws.stats.p,
-                                  ws.counters.p + 1, qsel.p);
-        HK_CHECK_LAUNCH();
-        HK_CHECK_CUDA(cudaStreamSynchronize(s));
-    }
-    if (nfb) {
-        long long add = nfb;
-        // host-side counter update
-        std::vector<long long> st(kStatSlots);
-        HK_CHECK_CUDA(cudaMemcpyAsync(st.data(), ws.stats.p, kStatSlots * sizeof(long long),
-                                      cudaMemcpyDeviceToHost, s));
-        HK_CHECK_CUDA(cudaStreamSynchronize(s));
-        st[ST_FALLBACK] += add;
-        HK_CHECK_CUDA(cudaMemcpyAsync(ws.stats.p, st.data(), kStatSlots * sizeof(long long),
-                                      cudaMemcpyHostToDevice, s));
-    }
 }
 
-void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s) {
+// Exhaustive answer for row q of Qd: collect every series at or below
+// T(U[q]), rescore and select into row q of ws.out_*.
+void exhaustive_one(Workspace &ws, const LeafView &v, const float *Qd, int q, uint32_t Ubits, int k,
+                    float rho, cudaStream_t s) {
+    const int sms = sm_count();
+    float u;
+    std::memcpy(&u, &Ubits, 4);
+    const float T = std::nextafter(u * (1.0f + rho), INFINITY);   // >= the device's T(U)
+    DevBuf<int32_t> cnt;
+    cnt.alloc(2, s);
+    HK_CHECK_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), s));
+    k_collect<<<sms * 16, 256, 0, s>>>(Qd, q, v.X, v.n, v.N, T, 0, cnt.p, nullptr, nullptr, 0);
+    HK_CHECK_LAUNCH();
+    int32_t c = 0;
+    HK_CHECK_CUDA(cudaMemcpyAsync(&c, cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (c < k) fail(HK_EINTERNAL, "exhaustive collection for query %d found %d < k candidates", q, c);
+    DevBuf<float> fd;
+    DevBuf<int32_t> fp;
+    DevBuf<double> fr;
+    DevBuf<int32_t> qsel;
+    fd.alloc(c, s);
+    fp.alloc(c, s);
+    fr.alloc(c, s);
+    qsel.alloc(1, s);
+    HK_CHECK_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t), s));
+    k_collect<<<sms * 16, 256, 0, s>>>(Qd, q, v.X, v.n, v.N, T, 1, cnt.p, fd.p, fp.p, c);
+    HK_CHECK_LAUNCH();
+    HK_CHECK_CUDA(cudaMemcpyAsync(qsel.p, &q, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    k_final<<<1, 256, 0, s>>>(Qd, v.X, v.n, v.perm, fd.p, fp.p, cnt.p, c, ws.U.p, nullptr, k, rho,
+                              fr.p, ws.out_ids.p, ws.out_dist.p, (long long *)ws.stats.p,
+                              ws.counters.p + 1, qsel.p);
+    HK_CHECK_LAUNCH();
+    int32_t err = 0;
+    HK_CHECK_CUDA(cudaMemcpyAsync(&err, ws.counters.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (err) fail(HK_EINTERNAL, "exhaustive collection for query %d: selection failed", q);
+}
+
+void add_host_stat(Workspace &ws, int slot, long long v, cudaStream_t s) {
+    std::vector<long long> st(kStatSlots);
+    HK_CHECK_CUDA(cudaMemcpyAsync(st.data(), ws.stats.p, kStatSlots * sizeof(long long),
+                                  cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    st[slot] += v;
+    HK_CHECK_CUDA(cudaMemcpyAsync(ws.stats.p, st.data(), kStatSlots * sizeof(long long),
+                                  cudaMemcpyHostToDevice, s));
+}
+
+void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s, ScanTimer *timer,
+                long long launches) {
     if (!stats) return;
     long long st[kStatSlots];
     HK_CHECK_CUDA(cudaMemcpyAsync(st, ws.stats.p, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -904,6 +977,10 @@ void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s) {
     stats->fallback_queries = st[ST_FALLBACK];
     stats->work_items = st[ST_ITEMS];
     stats->skip_sequential = st[ST_SKIPSEQ];
+    stats->scan_bytes = st[ST_SCAN_BYTES];
+    stats->retried_queries = st[ST_RETRIED];
+    stats->scan_ns = timer ? timer->total_ns() : 0;
+    stats->kernel_launches = launches;
 }
 
 __global__ void k_count_items_and_series(const int64_t *__restrict__ item_off, int64_t L,
@@ -931,9 +1008,14 @@ __global__ void k_count_items_and_series(const int64_t *__restrict__ item_off, i
 
 }  // namespace
 
-void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opts &o, cudaStream_t s,
-               int64_t *out_ids, float *out_dist, hk_query_stats *stats) {
-    Workspace &ws = idx->ws;
+namespace {
+
+// One pass of the query path over a batch (a1-a8 without the retries).
+// U_init: initial bounds (device, float bits) or nullptr for +inf; with
+// bounds given, the approximate search is skipped.
+void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, const hk_query_opts &o,
+                cudaStream_t s, const uint32_t *U_init, ScanTimer *timer, std::vector<int32_t> &flags,
+                std::vector<uint32_t> &Uh) {
     const int n = idx->n;
     const int64_t L = idx->L;
     const float rho = rho_for(n);
@@ -942,8 +1024,8 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
     const int l_max = o.l_max > 0 ? o.l_max : 1;
     const float eapca_th = o.eapca_th >= 0 ? o.eapca_th : 0.25f;
     ScanConfig cfg = choose_scan(n, k, !nosax, o.query_group);
-    const int S_T = o.series_tile > 0 ? o.series_tile : 2048;
-    const int pool_C = std::min(65536, std::max(2048, 32 * cfg.cap));
+    const int S_T = o.series_tile > 0 ? o.series_tile : 8192;
+    const int pool_C = std::min(65536, std::max(4096, 64 * cfg.cap));
 
     reserve_common(ws, nq, L, k, pool_C, s);
     ws.qseg.reserve((size_t)nq * idx->S * 2, s);
@@ -956,8 +1038,12 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
     HK_CHECK_CUDA(cudaMemsetAsync(ws.qflag.p, 0, nq * sizeof(int32_t), s));
     HK_CHECK_CUDA(cudaMemsetAsync(ws.qcand.p, 0, nq * sizeof(int32_t), s));
     HK_CHECK_CUDA(cudaMemsetAsync(ws.mask.p, 0, (size_t)L * nq, s));
-    k_fill_u32<<<64, 256, 0, s>>>(ws.U.p, nq, 0x7f800000u);
-    HK_CHECK_LAUNCH();
+    if (U_init) {
+        HK_CHECK_CUDA(cudaMemcpyAsync(ws.U.p, U_init, nq * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    } else {
+        k_fill_u32<<<64, 256, 0, s>>>(ws.U.p, nq, 0x7f800000u);
+        HK_CHECK_LAUNCH();
+    }
     {
         long long init[kStatSlots] = {0};
         init[ST_QUERIES] = nq;
@@ -967,7 +1053,7 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
 
     // a1 + a2
     k_qprep<<<nq, 256, n * sizeof(float), s>>>(Qd, n, idx->seg_ab.p, idx->S, idx->bp.p, ws.qseg.p,
-                                               nosax ? nullptr : ws.sax_tab.p);
+                                               nosax ? nullptr : reinterpret_cast<__half *>(ws.sax_tab.p));
     HK_CHECK_LAUNCH();
     k_lb_eapca<<<dim3((unsigned)((L + 127) / 128), std::min(nq, 65535)), 128, 0, s>>>(
         ws.qseg.p, idx->S, idx->leaf_nseg.p, idx->leaf_seg.p, idx->seg_ab.p, idx->env.p, L, nq,
@@ -987,7 +1073,7 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
     a.v = v;
     a.Q = Qd;
     a.nq = nq;
-    a.sax_tab = nosax ? nullptr : ws.sax_tab.p;
+    a.sax_tab = nosax ? nullptr : reinterpret_cast<const __half *>(ws.sax_tab.p);
     a.qmode = ws.qmode.p;
     a.lb = noprune ? nullptr : ws.lb.p;
     a.U = ws.U.p;
@@ -1005,14 +1091,14 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
     a.use_sax = nosax ? 0 : 1;
 
     // a3: approximate search (no LB_SAX: these leaves are scanned whole)
-    if (!noprune) {
+    if (!noprune && !U_init) {
         k_approx_select<<<nq, 256, 0, s>>>(ws.lb.p, L, idx->leaf_off.p, l_max, k, nq, kAmax, ws.approx.p,
                                            ws.qcand.p, ws.mask.p);
         HK_CHECK_LAUNCH();
         ScanArgs aa = a;
         aa.use_sax = 0;
         aa.lb = nullptr;
-        scan_phase(ws, v, aa, cfg, 1, nq, s);
+        scan_phase(ws, v, aa, cfg, 1, nq, s, timer);
         k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
                                                    (long long *)ws.stats.p, -1, ST_LEAVES_APPROX);
         HK_CHECK_LAUNCH();
@@ -1033,15 +1119,74 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
         HK_CHECK_LAUNCH();
     }
     // a5-a7: scan of the candidate leaves
-    scan_phase(ws, v, a, cfg, 2, nq, s);
+    scan_phase(ws, v, a, cfg, 2, nq, s, timer);
     k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
                                                (long long *)ws.stats.p, ST_SERIES_CAND, -1);
     HK_CHECK_LAUNCH();
     // a8: boundary rescore and answer
-    finish(ws, v, Qd, nq, k, pool_C, rho, s);
+    final_select(ws, v, Qd, nq, k, pool_C, rho, s, flags, Uh);
+}
+
+}  // namespace
+
+void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opts &o, cudaStream_t s,
+               int64_t *out_ids, float *out_dist, hk_query_stats *stats) {
+    Workspace &ws = idx->ws;
+    const long long launches0 = g_launches;
+    ScanTimer timer;
+    timer.on = (o.flags & HK_Q_TIMING) != 0;
+    std::vector<int32_t> flags;
+    std::vector<uint32_t> Uh;
+    query_pass(idx, ws, Qd, nq, k, o, s, nullptr, &timer, flags, Uh);
+
+    // Queries whose lists or pool overflowed: run them again starting from
+    // their final bound, which is tight, so far fewer candidates qualify.
+    std::vector<int32_t> sel;
+    for (int q = 0; q < nq; ++q)
+        if (flags[q] & 1) sel.push_back(q);
+    if (!sel.empty()) {
+        const int nsub = (int)sel.size();
+        Workspace &w2 = idx->ws_retry;
+        w2.Q.reserve((size_t)nsub * idx->n, s);
+        w2.Uinit.reserve(nsub, s);
+        w2.sel.reserve(nsub, s);
+        HK_CHECK_CUDA(cudaMemcpyAsync(w2.sel.p, sel.data(), nsub * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        k_gather_queries<<<nsub, 256, 0, s>>>(Qd, idx->n, w2.sel.p, nsub, ws.U.p, w2.Q.p, w2.Uinit.p);
+        HK_CHECK_LAUNCH();
+        std::vector<int32_t> flags2;
+        std::vector<uint32_t> U2;
+        query_pass(idx, w2, w2.Q.p, nsub, k, o, s, w2.Uinit.p, &timer, flags2, U2);
+        LeafView v;
+        v.X = idx->X.p;
+        v.perm = idx->perm.p;
+        v.sax = idx->sax.p;
+        v.leaf_off = idx->leaf_off.p;
+        v.N = idx->N;
+        v.n = idx->n;
+        v.L = idx->L;
+        long long exhaustive = 0;
+        for (int i = 0; i < nsub; ++i) {
+            if (!(flags2[i] & 1)) continue;
+            exhaustive_one(w2, v, w2.Q.p, i, U2[i], k, rho_for(idx->n), s);
+            ++exhaustive;
+        }
+        k_scatter_results<<<nsub, 128, 0, s>>>(w2.out_ids.p, w2.out_dist.p, w2.sel.p, nsub, k,
+                                               ws.out_ids.p, ws.out_dist.p);
+        HK_CHECK_LAUNCH();
+        // fold the retry's counters into the batch's
+        std::vector<long long> a(kStatSlots), b(kStatSlots);
+        HK_CHECK_CUDA(cudaMemcpyAsync(a.data(), ws.stats.p, kStatSlots * sizeof(long long), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaMemcpyAsync(b.data(), w2.stats.p, kStatSlots * sizeof(long long), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int i = ST_LEAVES_APPROX; i < kStatSlots; ++i)
+            if (i != ST_QUERIES && i != ST_LEAVES_TOTAL) a[i] += b[i];
+        a[ST_RETRIED] += nsub;
+        a[ST_FALLBACK] += exhaustive;
+        HK_CHECK_CUDA(cudaMemcpyAsync(ws.stats.p, a.data(), kStatSlots * sizeof(long long), cudaMemcpyHostToDevice, s));
+    }
     copy_out(ws, nq, k, out_ids, out_dist, s);
-    copy_stats(ws, stats, s);
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    copy_stats(ws, stats, s, &timer, g_launches - launches0);
 }
 
 void run_scan(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k, cudaStream_t s,
@@ -1050,7 +1195,7 @@ void run_scan(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,
     const float rho = rho_for(n);
     ScanConfig cfg = choose_scan(n, k, false, 0);
     const int S_T = 2048;
-    const int pool_C = std::min(65536, std::max(2048, 32 * cfg.cap));
+    const int pool_C = std::min(65536, std::max(4096, 64 * cfg.cap));
     reserve_common(ws, nq, 1, k, pool_C, s);
     DevBuf<int64_t> leaf_off;
     leaf_off.alloc(2, s);
@@ -1088,7 +1233,11 @@ void run_scan(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,
     a.stats = (long long *)ws.stats.p;
     a.use_sax = 0;
     scan_phase(ws, v, a, cfg, 2, nq, s);
-    finish(ws, v, Qd, nq, k, pool_C, rho, s);
+    std::vector<int32_t> flags;
+    std::vector<uint32_t> Uh;
+    final_select(ws, v, Qd, nq, k, pool_C, rho, s, flags, Uh);
+    for (int q = 0; q < nq; ++q)
+        if (flags[q] & 1) exhaustive_one(ws, v, Qd, q, Uh[q], k, rho, s);
     copy_out(ws, nq, k, out_ids, out_dist, s);
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
 }
@@ -1115,11 +1264,11 @@ void debug_lb_sax(hk_index *idx, const float *Qd, int nq, float *out_host) {
     Workspace &ws = idx->ws;
     ws.sax_tab.reserve((size_t)nq * kWord * kAlpha, s);
     k_qprep<<<nq, 256, idx->n * sizeof(float), s>>>(Qd, idx->n, idx->seg_ab.p, idx->S, idx->bp.p,
-                                                    nullptr, ws.sax_tab.p);
+                                                    nullptr, reinterpret_cast<__half *>(ws.sax_tab.p));
     HK_CHECK_LAUNCH();
     DevBuf<float> out;
     out.alloc((size_t)nq * idx->N, s);
-    k_debug_lbsax<<<dim3(256, std::min(nq, 65535)), 256, 0, s>>>(ws.sax_tab.p, idx->sax.p, idx->N, nq, out.p);
+    k_debug_lbsax<<<dim3(256, std::min(nq, 65535)), 256, 0, s>>>(reinterpret_cast<const __half *>(ws.sax_tab.p), idx->sax.p, idx->N, nq, out.p);
     HK_CHECK_LAUNCH();
     HK_CHECK_CUDA(cudaMemcpyAsync(out_host, out.p, (size_t)nq * idx->N * sizeof(float),
                                   cudaMemcpyDeviceToHost, s));

@@ -66,3 +66,17 @@ def test_argument_checks_without_gpu(hk):
                          ids.ctypes.data_as(ctypes.c_void_p),
                          d.ctypes.data_as(ctypes.c_void_p)) == hk.HK_EINVAL   # k > N
     assert L.hk_free(None) == hk.HK_OK
+
+
+def test_binding_structs_match_header(hk):
+    text = open(HEADER).read()
+
+    def fields(struct_name):
+        body = text[:text.index("} %s;" % struct_name)]
+        body = body[body.rindex("typedef struct {"):]
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        return re.findall(r"\b(?:u?int\d+_t|float|double)\s+(\w+)(?:\[\d+\])?;", body)
+
+    for cname, pyc in [("hk_build_opts", hk.hk_build_opts), ("hk_query_opts", hk.hk_query_opts),
+                       ("hk_query_stats", hk.hk_query_stats), ("hk_index_info", hk.hk_index_info)]:
+        assert [f[0] for f in pyc._fields_] == fields(cname), cname
