@@ -157,6 +157,30 @@ int hk_scan_knn(const float *X, int64_t N, int32_t n, const float *Q,
                 float *out_dist);
 
 /*
+ * hk_scan_knn_noalloc -- hk_scan_knn for callers that cannot allocate device
+ * memory.  The paper has no counterpart: it is an interface for callers
+ * that must not call cudaMalloc or cudaFree, e.g. a process whose device
+ * memory is held by another allocator (a framework's caching allocator can
+ * leave too little free for a raw cudaMalloc), or a latency-bound caller
+ * sharing the GPU (cudaFree waits for the whole device).
+ *
+ * Same answer definition as hk_scan_knn.  X (N*n), Q (nq*n), out_ids and
+ * out_dist (nq*k) must all be device memory; nothing is copied and nothing
+ * is allocated: the work space is a fixed 6 MiB array compiled into the
+ * library, held on every GPU that loads it until the process exits.
+ * Limits: 1 <= nq <= 64, 1 <= k <= min(N, 64), and at most 65,536
+ * near-tied candidates per query; larger sizes return HK_EINVAL (HK_ENOMEM
+ * for the tie limit) with a message.  The first call on a device looks up
+ * the array's device address and should come before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each
+ * call clears what must start at zero): calls whose GPU work overlaps, on
+ * different streams or host threads, race on it.
+ */
+int hk_scan_knn_noalloc(const float *X, int64_t N, int32_t n, const float *Q,
+                        int32_t nq, int32_t k, void *stream, int64_t *out_ids,
+                        float *out_dist);
+
+/*
  * hk_isax_breakpoints -- the 255 iSAX breakpoints the library uses
  * (Sec. 2: alphabet 256; beta_j the standard normal quantile of j/256),
  * as float32.  Host-only; needs no GPU.

@@ -71,6 +71,7 @@ _lib = None
 
 # every symbol include/hercules_gb300.h declares
 EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_scan_knn",
+           "hk_scan_knn_noalloc",
            "hk_isax_breakpoints", "hk_index_export", "hk_debug_lb_eapca", "hk_debug_lb_sax",
            "hk_last_error", "hk_version"]
 
@@ -94,6 +95,8 @@ def lib():
                                ctypes.POINTER(hk_query_stats)]
         L.hk_scan_knn.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, ctypes.c_int32,
                                   ctypes.c_int32, vp, vp, vp]
+        L.hk_scan_knn_noalloc.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, ctypes.c_int32,
+                                          ctypes.c_int32, vp, vp, vp]
         L.hk_isax_breakpoints.argtypes = [vp]
         L.hk_index_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.hk_debug_lb_eapca.argtypes = [vp, vp, ctypes.c_int32, vp]

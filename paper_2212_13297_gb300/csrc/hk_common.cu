@@ -193,6 +193,25 @@ __global__ void k_count_nonfinite(const float *__restrict__ p, int64_t count,
 }
 }  // namespace
 
+// Count NaN/Inf values into a caller-provided device counter (zeroed here)
+// and fail if there are any.  Synchronises the stream.
+void check_finite_with(const float *p, int64_t count, cudaStream_t s, const char *what,
+                       unsigned long long *dev_counter) {
+    if (count <= 0) return;
+    HK_CHECK_CUDA(cudaMemsetAsync(dev_counter, 0, sizeof(unsigned long long), s));
+    int dev = 0, sms = 0;
+    HK_CHECK_CUDA(cudaGetDevice(&dev));
+    HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+    k_count_nonfinite<<<(unsigned)blocks, 256, 0, s>>>(p, count, dev_counter);
+    HK_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    HK_CHECK_CUDA(cudaMemcpyAsync(&h, dev_counter, sizeof(h), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (h) fail(HK_EINVAL, "%s holds %llu NaN or Inf values", what, h);
+}
+
 void check_finite(const float *p, int64_t count, cudaStream_t s, const char *what) {
     if (count <= 0) return;
     DevBuf<unsigned long long> bad;

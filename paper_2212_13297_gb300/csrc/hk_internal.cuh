@@ -179,4 +179,34 @@ void run_scan(const float *Xdev, int64_t N, int n, const float *Qdev, int nq, in
 void debug_lb_eapca(hk_index *idx, const float *Qdev, int nq, double *out_host);
 void debug_lb_sax(hk_index *idx, const float *Qdev, int nq, float *out_host);
 void check_finite(const float *p, int64_t count, cudaStream_t s, const char *what);
+void check_finite_with(const float *p, int64_t count, cudaStream_t s, const char *what,
+                       unsigned long long *dev_counter);
+
+// Device buffers, carved by the caller from memory it already owns, for an
+// exhaustive scan that allocates nothing (see hk_noalloc.cu).
+struct ScanScratch {
+    uint32_t *U;             // nq
+    float *pool_d;           // nq * pool_C
+    int32_t *pool_p;         // nq * pool_C
+    double *rs_d;            // nq * pool_C
+    int32_t *pool_cnt;       // nq
+    int32_t *qflag;          // nq
+    int32_t *leaf_qoff;      // 2
+    int32_t *leaf_q;         // nq
+    int64_t *item_off;       // 2
+    int64_t *leaf_off;       // 2
+    int32_t *counters;       // 4
+    long long *stats;        // 24
+    float *col_d;            // col_cap
+    int32_t *col_p;          // col_cap
+    double *col_r;           // col_cap
+    int32_t *col_cnt;        // 2
+    int32_t *qsel;           // 1
+    int pool_C;
+    int col_cap;
+    int max_nq;
+};
+// Exhaustive exact k-NN into caller device buffers using only `sc`.
+void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,
+                      cudaStream_t s, int64_t *ids_dev, float *dist_dev, const ScanScratch &sc);
 }  // namespace hk

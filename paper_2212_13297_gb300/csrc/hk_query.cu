@@ -1242,6 +1242,103 @@ void run_scan(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
 }
 
+void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,
+                      cudaStream_t s, int64_t *ids_dev, float *dist_dev, const ScanScratch &sc) {
+    const float rho = rho_for(n);
+    ScanConfig cfg = choose_scan(n, k, false, 0);
+    const int S_T = 2048;
+    // the single-leaf work list, built on the host (stack arrays only)
+    int32_t h_qoff[2] = {0, nq};
+    int32_t h_q[64];
+    for (int q = 0; q < nq; ++q) h_q[q] = q;
+    const int64_t items = (int64_t)((nq + cfg.G - 1) / cfg.G) * ((N + S_T - 1) / S_T);
+    int64_t h_item_off[2] = {0, items};
+    int64_t h_leaf_off[2] = {0, N};
+    HK_CHECK_CUDA(cudaMemcpyAsync(sc.leaf_qoff, h_qoff, sizeof(h_qoff), cudaMemcpyHostToDevice, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(sc.leaf_q, h_q, nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(sc.item_off, h_item_off, sizeof(h_item_off), cudaMemcpyHostToDevice, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(sc.leaf_off, h_leaf_off, sizeof(h_leaf_off), cudaMemcpyHostToDevice, s));
+    // the scratch keeps the previous call's contents: clear what must start at zero
+    HK_CHECK_CUDA(cudaMemsetAsync(sc.pool_cnt, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(sc.qflag, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(sc.counters, 0, 4 * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(sc.stats, 0, kStatSlots * sizeof(long long), s));
+    k_fill_u32<<<1, 64, 0, s>>>(sc.U, nq, 0x7f800000u);
+    HK_CHECK_LAUNCH();
+    LeafView v;
+    v.X = Xd;
+    v.perm = nullptr;
+    v.sax = nullptr;
+    v.leaf_off = sc.leaf_off;
+    v.N = N;
+    v.n = n;
+    v.L = 1;
+    ScanArgs a{};
+    a.v = v;
+    a.Q = Qd;
+    a.nq = nq;
+    a.U = sc.U;
+    a.leaf_qoff = sc.leaf_qoff;
+    a.leaf_q = sc.leaf_q;
+    a.item_off = sc.item_off;
+    a.work_ctr = sc.counters;
+    a.S_T = S_T;
+    a.k = k;
+    a.cap = cfg.cap;
+    a.p2 = cfg.p2;
+    a.rho = rho;
+    a.pool_d = sc.pool_d;
+    a.pool_p = sc.pool_p;
+    a.pool_cnt = sc.pool_cnt;
+    a.pool_C = sc.pool_C;
+    a.qflag = sc.qflag;
+    a.stats = sc.stats;
+    a.use_sax = 0;
+    launch_scan(a, cfg, s);
+    k_pool_kth<<<nq, 256, 0, s>>>(sc.pool_d, sc.pool_cnt, sc.pool_C, k, rho, sc.U);
+    HK_CHECK_LAUNCH();
+    k_final<<<nq, 256, 0, s>>>(Qd, Xd, n, nullptr, sc.pool_d, sc.pool_p, sc.pool_cnt, sc.pool_C, sc.U,
+                               sc.qflag, k, rho, sc.rs_d, ids_dev, dist_dev, sc.stats, sc.counters + 1,
+                               nullptr);
+    HK_CHECK_LAUNCH();
+    int32_t flags[64];
+    uint32_t U[64];
+    int32_t err = 0;
+    HK_CHECK_CUDA(cudaMemcpyAsync(flags, sc.qflag, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(U, sc.U, nq * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(&err, sc.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (err) fail(HK_EINTERNAL, "a query had fewer than k candidates after the scan");
+    const int sms = sm_count();
+    for (int q = 0; q < nq; ++q) {
+        if (!(flags[q] & 1)) continue;
+        // more near-ties than the lists hold: collect every series at or
+        // below the final bound into the scratch's collection area
+        float u;
+        std::memcpy(&u, &U[q], 4);
+        const float T = std::nextafter(u * (1.0f + rho), INFINITY);
+        HK_CHECK_CUDA(cudaMemsetAsync(sc.col_cnt, 0, 2 * sizeof(int32_t), s));
+        k_collect<<<sms * 16, 256, 0, s>>>(Qd, q, Xd, n, N, T, 1, sc.col_cnt, sc.col_d, sc.col_p,
+                                           sc.col_cap);
+        HK_CHECK_LAUNCH();
+        int32_t c = 0;
+        HK_CHECK_CUDA(cudaMemcpyAsync(&c, sc.col_cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (c > sc.col_cap)
+            fail(HK_ENOMEM, "query %d has %d near-tied candidates; the fixed scratch holds %d", q, c,
+                 sc.col_cap);
+        HK_CHECK_CUDA(cudaMemcpyAsync(sc.qsel, &q, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        k_final<<<1, 256, 0, s>>>(Qd, Xd, n, nullptr, sc.col_d, sc.col_p, sc.col_cnt, c, sc.U, nullptr,
+                                  k, rho, sc.col_r, ids_dev, dist_dev, sc.stats, sc.counters + 1,
+                                  sc.qsel);
+        HK_CHECK_LAUNCH();
+        HK_CHECK_CUDA(cudaMemcpyAsync(&err, sc.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (err) fail(HK_EINTERNAL, "selection failed for query %d", q);
+    }
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
 void debug_lb_eapca(hk_index *idx, const float *Qd, int nq, double *out_host) {
     cudaStream_t s = idx->stream;
     Workspace &ws = idx->ws;
