@@ -184,6 +184,8 @@ def main():
     ap.add_argument("--query-group", type=int, default=0)
     ap.add_argument("--series-tile", type=int, default=0)
     ap.add_argument("--l-max", type=int, default=0)
+    ap.add_argument("--form", default="plain", choices=["plain", "bf16"],
+                    help="plain float32 scan, or the bfloat16 tensor-core form")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
@@ -217,7 +219,9 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sample = X[:min(N, 4_000_000)].cpu().numpy()
     t0 = time.perf_counter()
-    idx = binding.Index(X, wl["tau"])
+    bflags = binding.HK_BUILD_BF16 if args.form == "bf16" else 0
+    qflags = binding.HK_Q_TIMING | (binding.HK_Q_BF16 if args.form == "bf16" else 0)
+    idx = binding.Index(X, wl["tau"], flags=bflags)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
     info = idx.info()
@@ -231,7 +235,7 @@ def main():
     qkw = dict(l_max=args.l_max, query_group=args.query_group, series_tile=args.series_tile)
 
     for i in range(args.warmup):
-        idx.query(batches[i], k, flags=binding.HK_Q_TIMING, out=(ids, dist_out), **qkw)
+        idx.query(batches[i], k, flags=qflags, out=(ids, dist_out), **qkw)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(dev_index)
@@ -246,7 +250,7 @@ def main():
     step_lat, agg = [], {}
     for i in range(args.steps):
         ts = time.perf_counter()
-        _, _, st = idx.query(batches[args.warmup + i], k, flags=binding.HK_Q_TIMING,
+        _, _, st = idx.query(batches[args.warmup + i], k, flags=qflags,
                              out=(ids, dist_out), **qkw)
         step_lat.append(time.perf_counter() - ts)
         for key, v in st.items():
@@ -275,7 +279,7 @@ def main():
             torch.distributed.barrier()
         te = time.perf_counter()
         for i in range(args.steps):
-            idx.query(hq[i], k, out=(hid, hdi), **qkw)
+            idx.query(hq[i], k, flags=qflags & ~binding.HK_Q_TIMING, out=(hid, hdi), **qkw)
         t_e2e = time.perf_counter() - te
         if ws > 1:
             t = torch.tensor([t_e2e], device="cuda")

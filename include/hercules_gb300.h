@@ -97,6 +97,10 @@ int hk_index_info_get(const hk_index *idx, hk_index_info *out);
 #define HK_Q_NOPRUNE 4u    /* scan every series (parallel-scan baseline)      */
 #define HK_Q_TIMING 8u     /* time the scan kernels with CUDA events on the
                               call's stream (hk_query_stats.scan_ns)          */
+#define HK_Q_BF16 16u      /* precision form: distances of the candidate
+                              leaves on the tensor cores from the bfloat16
+                              copy (index built with HK_BUILD_BF16, n <= 256),
+                              certified error bound, exact rescore           */
 
 typedef struct {
     int32_t l_max;        /* leaves visited by the approximate search per query
@@ -128,6 +132,8 @@ typedef struct {
     int64_t kernel_launches;      /* kernels this call launched                  */
     int64_t scan_bytes;           /* series bytes the scan read: 64 B per 16-point
                                      chunk loaded + 16 B per iSAX word, per item */
+    int64_t tc_pairs;             /* (query, series) distances on tensor cores   */
+    int64_t tc_candidates;        /* of those, kept for the exact rescore        */
 } hk_query_stats;
 
 /*
@@ -216,6 +222,14 @@ int hk_debug_lb_eapca(hk_index *idx, const float *Q, int32_t nq, double *out);
  * out[q*N + pos].  Q host or device; out host.
  */
 int hk_debug_lb_sax(hk_index *idx, const float *Q, int32_t nq, float *out);
+
+/*
+ * hk_debug_tc_dist -- the tensor-core form's D~(q, x) = |q|^2 + |x|^2 - 2 q^.x^
+ * (bfloat16 operands, float32 accumulation) for every query and every series
+ * in leaf order, dt[q*N + pos], and the certified bound E(q, x) the filter
+ * uses, err[q*N + pos] (index built with HK_BUILD_BF16).  Host outputs.
+ */
+int hk_debug_tc_dist(hk_index *idx, const float *Q, int32_t nq, float *dt, float *err);
 
 const char *hk_last_error(void);
 const char *hk_version(void);

@@ -29,6 +29,7 @@ HK_Q_NOSAX = 1
 HK_Q_NOTHRESH = 2
 HK_Q_NOPRUNE = 4
 HK_Q_TIMING = 8
+HK_Q_BF16 = 16
 
 
 class hk_build_opts(ctypes.Structure):
@@ -47,7 +48,7 @@ class hk_query_stats(ctypes.Structure):
         "queries", "leaves_total", "leaves_approx", "leaves_candidate", "series_candidate",
         "series_sax_pruned", "series_abandoned", "series_full", "points_computed", "rescored",
         "fallback_queries", "retried_queries", "work_items", "skip_sequential", "scan_ns", "kernel_launches",
-        "scan_bytes")]
+        "scan_bytes", "tc_pairs", "tc_candidates")]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -73,6 +74,7 @@ _lib = None
 EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_scan_knn",
            "hk_scan_knn_noalloc",
            "hk_isax_breakpoints", "hk_index_export", "hk_debug_lb_eapca", "hk_debug_lb_sax",
+           "hk_debug_tc_dist",
            "hk_last_error", "hk_version"]
 
 
@@ -101,6 +103,7 @@ def lib():
         L.hk_index_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.hk_debug_lb_eapca.argtypes = [vp, vp, ctypes.c_int32, vp]
         L.hk_debug_lb_sax.argtypes = [vp, vp, ctypes.c_int32, vp]
+        L.hk_debug_tc_dist.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
         L.hk_last_error.restype = ctypes.c_char_p
         L.hk_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -218,6 +221,13 @@ class Index:
         out = np.empty((Q.shape[0], L), np.float64)
         _check(lib().hk_debug_lb_eapca(self._h, _ptr(Q), Q.shape[0], _ptr(out)))
         return out
+
+    def debug_tc_dist(self, Q):
+        """(D~ [nq, N], E [nq, N]) from the tensor-core kernel, leaf order."""
+        dt = np.empty((Q.shape[0], self.N), np.float32)
+        err = np.empty((Q.shape[0], self.N), np.float32)
+        _check(lib().hk_debug_tc_dist(self._h, _ptr(Q), Q.shape[0], _ptr(dt), _ptr(err)))
+        return dt, err
 
     def debug_lb_sax(self, Q):
         out = np.empty((Q.shape[0], self.N), np.float32)

@@ -112,7 +112,8 @@ int hk_index_info_get(const hk_index *idx, hk_index_info *out) {
                                       idx->leaf_off.bytes() + idx->leaf_nseg.bytes() +
                                       idx->leaf_seg.bytes() + idx->env.bytes() +
                                       idx->seg_ab.bytes() + idx->bp.bytes());
-        out->has_bf16 = 0;
+        out->has_bf16 = idx->has_bf16 ? 1 : 0;
+        out->device_bytes += (int64_t)(idx->Xb.bytes() + idx->x2.bytes() + idx->xn.bytes());
     });
 }
 
@@ -133,6 +134,12 @@ int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k, const hk_quer
         }
         if (o.l_max < 0) hk::fail(HK_EINVAL, "l_max=%d must be >= 0", o.l_max);
         if (o.query_group < 0 || o.series_tile < 0) hk::fail(HK_EINVAL, "tile sizes must be >= 0");
+        if (o.flags & HK_Q_BF16) {
+            if (!idx->has_bf16) hk::fail(HK_EINVAL, "HK_Q_BF16 needs an index built with HK_BUILD_BF16");
+            if (idx->n > hk::kTcMaxLen)
+                hk::fail(HK_EINVAL, "HK_Q_BF16 takes series of length <= %d (n=%d)", hk::kTcMaxLen, idx->n);
+            if (o.flags & HK_Q_NOPRUNE) hk::fail(HK_EINVAL, "HK_Q_BF16 and HK_Q_NOPRUNE exclude each other");
+        }
         cudaStream_t s = (cudaStream_t)stream;
         idx->stream = s;
         hk::DevBuf<float> tmp;
@@ -193,6 +200,17 @@ int hk_debug_lb_sax(hk_index *idx, const float *Q, int32_t nq, float *out) {
         hk::DevBuf<float> tmp;
         const float *Qd = device_view(Q, (size_t)nq * idx->n, idx->stream, tmp);
         hk::debug_lb_sax(idx, Qd, nq, out);
+    });
+}
+
+int hk_debug_tc_dist(hk_index *idx, const float *Q, int32_t nq, float *dt, float *err) {
+    return guard([&] {
+        if (!idx || !Q || !dt || !err || nq < 1) hk::fail(HK_EINVAL, "bad argument");
+        if (!idx->has_bf16) hk::fail(HK_EINVAL, "index built without HK_BUILD_BF16");
+        if (idx->n > hk::kTcMaxLen) hk::fail(HK_EINVAL, "n=%d > %d", idx->n, hk::kTcMaxLen);
+        hk::DevBuf<float> tmp;
+        const float *Qd = device_view(Q, (size_t)nq * idx->n, idx->stream, tmp);
+        hk::debug_tc_dist(idx, Qd, nq, dt, err);
     });
 }
 

@@ -658,6 +658,16 @@ void build_index(hk_index *idx, const float *Xsrc, int64_t N, int n, const hk_bu
     idx->sax.alloc((size_t)N * kWord, s);
     k_isax<<<grid_for(N, 256, sms), 256, 0, s>>>(idx->X.p, n, N, idx->bp.p, idx->sax.p);
     HK_CHECK_LAUNCH();
+    if (o.flags & HK_BUILD_BF16) {
+        // bfloat16 copy for the tensor-core form: rows padded so a 128-series
+        // tile starting at any 8-aligned position stays inside the buffer
+        idx->Npad = ((N + 7) / 8) * 8 + 136;
+        idx->Xb.alloc((size_t)idx->Npad * n, s);
+        idx->x2.alloc(idx->Npad, s);
+        idx->xn.alloc(idx->Npad, s);
+        launch_make_bf16(idx->X.p, N, n, idx->Npad, idx->Xb.p, idx->x2.p, idx->xn.p, s);
+        idx->has_bf16 = true;
+    }
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -118,6 +118,11 @@ struct Workspace {
     DevBuf<int64_t> out_ids;    // nq * k
     DevBuf<float> out_dist;     // nq * k
     DevBuf<int32_t> approx;     // nq * A
+    DevBuf<uint16_t> Qb;        // bfloat16 queries (tensor-core form)
+    DevBuf<float> q2, qa;       // query squared norms, error coefficients
+    DevBuf<int32_t> cand_cnt;   // nq    tensor-core candidates per query
+    DevBuf<int32_t> cand_p;     // nq * cand_C
+    DevBuf<float> cand_lb;      // nq * cand_C  lower bound D~ - E
     DevBuf<uint32_t> Uinit;     // retry pass: starting bounds
     DevBuf<int32_t> sel;        // retry pass: rows of the batch it answers
 };
@@ -157,6 +162,10 @@ struct hk_index {
     hk::DevBuf<double> env;        // L*kMaxSeg*4
     hk::DevBuf<int32_t> seg_ab;    // S*2  (a, b)
     hk::DevBuf<float> bp;          // 255 breakpoints
+    hk::DevBuf<uint16_t> Xb;       // bfloat16 copy in core-matrix order (HK_BUILD_BF16)
+    hk::DevBuf<float> x2, xn;      // squared norms and norms of the float32 rows
+    int64_t Npad = 0;
+    bool has_bf16 = false;
 
     std::vector<int64_t> h_leaf_off;
     std::vector<int32_t> h_leaf_nseg;
@@ -178,6 +187,7 @@ void run_scan(const float *Xdev, int64_t N, int n, const float *Qdev, int nq, in
               cudaStream_t s, int64_t *out_ids, float *out_dist);
 void debug_lb_eapca(hk_index *idx, const float *Qdev, int nq, double *out_host);
 void debug_lb_sax(hk_index *idx, const float *Qdev, int nq, float *out_host);
+void debug_tc_dist(hk_index *idx, const float *Qdev, int nq, float *dt_host, float *err_host);
 void check_finite(const float *p, int64_t count, cudaStream_t s, const char *what);
 void check_finite_with(const float *p, int64_t count, cudaStream_t s, const char *what,
                        unsigned long long *dev_counter);
@@ -206,6 +216,47 @@ struct ScanScratch {
     int col_cap;
     int max_nq;
 };
+// Arguments of the tensor-core distance scan (hk_tc.cu).
+struct TcArgs {
+    const uint16_t *Xb;          // bfloat16 collection, core-matrix order, padded rows
+    const float *x2, *xn;        // per position: squared norm, norm (rounded up)
+    int n;
+    const uint16_t *Qb;          // bfloat16 queries, row-major
+    const float *q2, *qa;        // per query: squared norm, error coefficient * norm
+    float eb;                    // relative error coefficient on |q|^2 + |x|^2
+    const int64_t *leaf_off;
+    int64_t L;
+    const int32_t *leaf_qoff, *leaf_q;
+    const int64_t *item_off;
+    int32_t *work_ctr;
+    int S_T;
+    uint32_t *U;
+    int k;
+    int32_t *cand_cnt, *cand_p;
+    float *cand_lb;
+    int cand_C;
+    int32_t *qflag;
+    int32_t *err;
+    long long *stats;
+    int stat_pairs, stat_cands;
+    uint32_t idesc;
+    float *dbg;                  // if set: D~ of every pair, dbg[q * N + pos]
+    int64_t N;
+};
+void launch_tc_scan(const TcArgs &a, cudaStream_t s);
+void launch_make_bf16(const float *X, int64_t N, int n, int64_t Npad, void *Xb, float *x2, float *xn,
+                      cudaStream_t s);
+void launch_tc_qprep(const float *Q, int nq, int n, double c_rel, void *Qb, float *q2, float *qa,
+                     cudaStream_t s);
+void launch_tc_rescore(const float *Q, const float *X, int n, int nq, const int32_t *cand_cnt,
+                       const int32_t *cand_p, const float *cand_lb, int cand_C, const uint32_t *U,
+                       float *pool_d, int32_t *pool_p, int32_t *pool_cnt, int pool_C, int32_t *qflag,
+                       long long *stats, int stat_slot, cudaStream_t s);
+size_t tc_smem_bytes(int n);
+uint32_t tc_idesc();
+double tc_error_coefficient(int n);
+constexpr int kTcMaxLen = 256;     // longest series the tensor-core form takes
+
 // Exhaustive exact k-NN into caller device buffers using only `sc`.
 void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,
                       cudaStream_t s, int64_t *ids_dev, float *dist_dev, const ScanScratch &sc);

@@ -53,7 +53,8 @@ constexpr int kAmax = 256;     // most leaves the approximate step visits
 enum StatIdx {
     ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_APPROX, ST_LEAVES_CAND, ST_SERIES_CAND,
     ST_SAX_PRUNED, ST_ABANDONED, ST_FULL, ST_POINTS, ST_RESCORED, ST_FALLBACK,
-    ST_ITEMS, ST_SKIPSEQ, ST_SCAN_NS, ST_LAUNCHES, ST_SCAN_BYTES, ST_RETRIED
+    ST_ITEMS, ST_SKIPSEQ, ST_SCAN_NS, ST_LAUNCHES, ST_SCAN_BYTES, ST_RETRIED, ST_TC_PAIRS,
+    ST_TC_CANDS
 };
 
 struct ScanArgs {
@@ -834,17 +835,23 @@ struct ScanTimer {
 };
 
 // Build leaf-major lists for mask value v and run the scan over them.
-void scan_phase(Workspace &ws, const LeafView &v, ScanArgs a, const ScanConfig &c, uint8_t val,
-                int nq, cudaStream_t s, ScanTimer *timer = nullptr) {
+// Leaf-major work lists for mask value `val`: per leaf the queries for which
+// it is a candidate, and work items of G queries x S_T series.
+void build_lists(Workspace &ws, const LeafView &v, int G, int S_T, uint8_t val, int nq, cudaStream_t s) {
     const int64_t L = v.L;
-    k_leaf_count<<<(unsigned)L, 256, 0, s>>>(ws.mask.p, nq, val, v.leaf_off, c.G, a.S_T,
-                                            ws.leaf_qcnt.p, ws.leaf_items.p);
+    k_leaf_count<<<(unsigned)L, 256, 0, s>>>(ws.mask.p, nq, val, v.leaf_off, G, S_T, ws.leaf_qcnt.p,
+                                            ws.leaf_items.p);
     HK_CHECK_LAUNCH();
     exclusive_scan_i32(ws.leaf_qcnt.p, ws.leaf_qoff.p, L, s, ws.scan_tmp32);
     exclusive_scan_i64(ws.leaf_items.p, ws.item_off.p, L, s, ws.scan_tmp64);
     k_leaf_fill<<<(unsigned)L, 256, 0, s>>>(ws.mask.p, nq, val, ws.leaf_qoff.p, ws.leaf_q.p);
     HK_CHECK_LAUNCH();
     HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p, 0, sizeof(int32_t), s));
+}
+
+void scan_phase(Workspace &ws, const LeafView &v, ScanArgs a, const ScanConfig &c, uint8_t val,
+                int nq, cudaStream_t s, ScanTimer *timer = nullptr) {
+    build_lists(ws, v, c.G, a.S_T, val, nq, s);
     a.leaf_qoff = ws.leaf_qoff.p;
     a.leaf_q = ws.leaf_q.p;
     a.item_off = ws.item_off.p;
@@ -979,6 +986,8 @@ void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s, Scan
     stats->skip_sequential = st[ST_SKIPSEQ];
     stats->scan_bytes = st[ST_SCAN_BYTES];
     stats->retried_queries = st[ST_RETRIED];
+    stats->tc_pairs = st[ST_TC_PAIRS];
+    stats->tc_candidates = st[ST_TC_CANDS];
     stats->scan_ns = timer ? timer->total_ns() : 0;
     stats->kernel_launches = launches;
 }
@@ -1020,7 +1029,8 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     const int64_t L = idx->L;
     const float rho = rho_for(n);
     const bool noprune = (o.flags & HK_Q_NOPRUNE) != 0;
-    const bool nosax = noprune || (o.flags & HK_Q_NOSAX) != 0;
+    const bool tc = (o.flags & HK_Q_BF16) != 0;
+    const bool nosax = noprune || tc || (o.flags & HK_Q_NOSAX) != 0;
     const int l_max = o.l_max > 0 ? o.l_max : 1;
     const float eapca_th = o.eapca_th >= 0 ? o.eapca_th : 0.25f;
     ScanConfig cfg = choose_scan(n, k, !nosax, o.query_group);
@@ -1051,6 +1061,12 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         HK_CHECK_CUDA(cudaMemcpyAsync(ws.stats.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
     }
 
+    if (tc) {
+        ws.Qb.reserve((size_t)nq * n, s);
+        ws.q2.reserve(nq, s);
+        ws.qa.reserve(nq, s);
+        launch_tc_qprep(Qd, nq, n, tc_error_coefficient(n), ws.Qb.p, ws.q2.p, ws.qa.p, s);
+    }
     // a1 + a2
     k_qprep<<<nq, 256, n * sizeof(float), s>>>(Qd, n, idx->seg_ab.p, idx->S, idx->bp.p, ws.qseg.p,
                                                nosax ? nullptr : reinterpret_cast<__half *>(ws.sax_tab.p));
@@ -1119,7 +1135,62 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         HK_CHECK_LAUNCH();
     }
     // a5-a7: scan of the candidate leaves
-    scan_phase(ws, v, a, cfg, 2, nq, s, timer);
+    if (tc) {
+        // a9: tensor-core distances with a certified bound, then the exact
+        // float32 rescore of the survivors into the pool
+        const int cand_C = std::max(4096, 256 * k);
+        ws.cand_cnt.reserve(nq, s);
+        ws.cand_p.reserve((size_t)nq * cand_C, s);
+        ws.cand_lb.reserve((size_t)nq * cand_C, s);
+        HK_CHECK_CUDA(cudaMemsetAsync(ws.cand_cnt.p, 0, nq * sizeof(int32_t), s));
+        HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p + 2, 0, sizeof(int32_t), s));
+        const int S_tc = o.series_tile > 0 ? o.series_tile : 16384;
+        build_lists(ws, v, 128, S_tc, 2, nq, s);
+        TcArgs t{};
+        t.Xb = idx->Xb.p;
+        t.x2 = idx->x2.p;
+        t.xn = idx->xn.p;
+        t.n = n;
+        t.Qb = ws.Qb.p;
+        t.q2 = ws.q2.p;
+        t.qa = ws.qa.p;
+        t.eb = (float)(std::ldexp(1.0, -19) * (1.0 + std::ldexp(1.0, -10)));
+        t.leaf_off = v.leaf_off;
+        t.L = L;
+        t.leaf_qoff = ws.leaf_qoff.p;
+        t.leaf_q = ws.leaf_q.p;
+        t.item_off = ws.item_off.p;
+        t.work_ctr = ws.counters.p;
+        t.S_T = S_tc;
+        t.U = ws.U.p;
+        t.k = k;
+        t.cand_cnt = ws.cand_cnt.p;
+        t.cand_p = ws.cand_p.p;
+        t.cand_lb = ws.cand_lb.p;
+        t.cand_C = cand_C;
+        t.qflag = ws.qflag.p;
+        t.err = ws.counters.p + 2;
+        t.stats = (long long *)ws.stats.p;
+        t.stat_pairs = ST_TC_PAIRS;
+        t.stat_cands = ST_TC_CANDS;
+        t.idesc = tc_idesc();
+        t.dbg = nullptr;
+        t.N = idx->N;
+        if (timer) timer->mark(s);
+        launch_tc_scan(t, s);
+        if (timer) timer->mark(s);
+        k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+        HK_CHECK_LAUNCH();
+        launch_tc_rescore(Qd, v.X, n, nq, ws.cand_cnt.p, ws.cand_p.p, ws.cand_lb.p, cand_C, ws.U.p,
+                          ws.pool_d.p, ws.pool_p.p, ws.pool_cnt.p, pool_C, ws.qflag.p,
+                          (long long *)ws.stats.p, ST_FULL, s);
+        int32_t terr = 0;
+        HK_CHECK_CUDA(cudaMemcpyAsync(&terr, ws.counters.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (terr) fail(HK_ETIMEOUT, "tensor-core scan: a bounded wait ran out (flag %d)", terr);
+    } else {
+        scan_phase(ws, v, a, cfg, 2, nq, s, timer);
+    }
     k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
                                                (long long *)ws.stats.p, ST_SERIES_CAND, -1);
     HK_CHECK_LAUNCH();
@@ -1337,6 +1408,81 @@ void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq
         if (err) fail(HK_EINTERNAL, "selection failed for query %d", q);
     }
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+// D~ for every (query, series) pair from the tensor-core kernel, and the
+// certified bound E that the filter uses, for tests of the bound.
+void debug_tc_dist(hk_index *idx, const float *Qd, int nq, float *dt_host, float *err_host) {
+    cudaStream_t s = idx->stream;
+    Workspace ws;
+    const int n = idx->n;
+    const int64_t L = idx->L, N = idx->N;
+    ws.Qb.reserve((size_t)nq * n, s);
+    ws.q2.reserve(nq, s);
+    ws.qa.reserve(nq, s);
+    launch_tc_qprep(Qd, nq, n, tc_error_coefficient(n), ws.Qb.p, ws.q2.p, ws.qa.p, s);
+    reserve_common(ws, nq, L, 1, 1, s);
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.mask.p, 2, (size_t)L * nq, s));
+    k_fill_u32<<<64, 256, 0, s>>>(ws.U.p, nq, 0x7f800000u);
+    HK_CHECK_LAUNCH();
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.qflag.p, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p, 0, 4 * sizeof(int32_t), s));
+    LeafView v;
+    v.leaf_off = idx->leaf_off.p;
+    v.L = L;
+    const int S_tc = 4096;
+    build_lists(ws, v, 128, S_tc, 2, nq, s);
+    const int cand_C = 1;
+    ws.cand_cnt.reserve(nq, s);
+    ws.cand_p.reserve((size_t)nq * cand_C, s);
+    ws.cand_lb.reserve((size_t)nq * cand_C, s);
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.cand_cnt.p, 0, nq * sizeof(int32_t), s));
+    DevBuf<float> dbg;
+    dbg.alloc((size_t)nq * N, s);
+    HK_CHECK_CUDA(cudaMemsetAsync(dbg.p, 0xff, (size_t)nq * N * sizeof(float), s));   // NaN
+    TcArgs t{};
+    t.Xb = idx->Xb.p;
+    t.x2 = idx->x2.p;
+    t.xn = idx->xn.p;
+    t.n = n;
+    t.Qb = ws.Qb.p;
+    t.q2 = ws.q2.p;
+    t.qa = ws.qa.p;
+    t.eb = (float)(std::ldexp(1.0, -19) * (1.0 + std::ldexp(1.0, -10)));
+    t.leaf_off = v.leaf_off;
+    t.L = L;
+    t.leaf_qoff = ws.leaf_qoff.p;
+    t.leaf_q = ws.leaf_q.p;
+    t.item_off = ws.item_off.p;
+    t.work_ctr = ws.counters.p;
+    t.S_T = S_tc;
+    t.U = ws.U.p;
+    t.k = 1;
+    t.cand_cnt = ws.cand_cnt.p;
+    t.cand_p = ws.cand_p.p;
+    t.cand_lb = ws.cand_lb.p;
+    t.cand_C = cand_C;
+    t.qflag = ws.qflag.p;
+    t.err = ws.counters.p + 2;
+    t.stats = nullptr;
+    t.idesc = tc_idesc();
+    t.dbg = dbg.p;
+    t.N = N;
+    launch_tc_scan(t, s);
+    int32_t terr = 0;
+    HK_CHECK_CUDA(cudaMemcpyAsync(&terr, ws.counters.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(dt_host, dbg.p, (size_t)nq * N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    // the bound: qa[q] * xn[pos] + eb * (q2[q] + x2[pos])
+    std::vector<float> q2(nq), qa(nq), x2(N), xn(N);
+    HK_CHECK_CUDA(cudaMemcpyAsync(q2.data(), ws.q2.p, nq * 4, cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(qa.data(), ws.qa.p, nq * 4, cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(x2.data(), idx->x2.p, N * 4, cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(xn.data(), idx->xn.p, N * 4, cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (terr) fail(HK_ETIMEOUT, "tensor-core scan: a bounded wait ran out (flag %d)", terr);
+    for (int q = 0; q < nq; ++q)
+        for (int64_t p = 0; p < N; ++p)
+            err_host[(int64_t)q * N + p] = qa[q] * xn[p] + t.eb * (q2[q] + x2[p]);
 }
 
 void debug_lb_eapca(hk_index *idx, const float *Qd, int nq, double *out_host) {

@@ -1,0 +1,557 @@
+// Precision form: squared distances on the tcgen05 tensor cores.
+//
+// For a block of up to 128 queries and a run of series, D~(q,x) =
+// |q|^2 + |x|^2 - 2 q^.x^ with q^, x^ the bfloat16 roundings and the dot
+// products accumulated in float32 in tensor memory.  Each D~ carries a
+// certified error bound E(q,x) = A_q |x| + B (|q|^2 + |x|^2):
+//   |q^.x^ - q.x| <= (2u + u^2 + g(1+u)^2) |q||x|,  u = 2^-8 (bfloat16),
+//   g = n w / (1 - n w), w = 2^-20 (a pessimistic per-addition error of the
+//   float32 accumulation, allowing truncating adders),
+// doubled for the -2 factor, plus a relative term covering the float32
+// rounding of the norms and of the epilogue arithmetic.  A series stays a
+// candidate of a query while D~ - E <= U (U bounds the query's true k-th
+// distance); D~ + E of k series bounds it from above, so each query's row
+// keeps its k smallest D~ + E and tightens U with them.  Candidates are
+// rescored exactly afterwards, so the answer stays exact.
+//
+// Data layout.  The bfloat16 copy of the collection is stored in the
+// tensor core's no-swizzle K-major "core matrix" order: series are grouped
+// by 8 (leaf order); a group is n/8 blocks of 8 series x 8 points (128 bytes),
+// block k holding points 8k..8k+7.  A tile of 128 consecutive series (16
+// groups, 8-aligned) is then one contiguous run of 128*n*2 bytes that a
+// single bulk copy (cp.async.bulk) places in shared memory in exactly the
+// layout the MMA descriptor describes: leading-dimension offset 128 bytes
+// (next 8 points), stride-dimension offset (n/8)*128 bytes (next 8 series).
+// The query block is gathered into the same layout with ordinary stores.
+//
+// CTA roles (6 warps): warp 0 issues the bulk copies, warp 1 (one thread)
+// issues tcgen05.mma and tcgen05.commit, warps 2-5 (128 threads, one per
+// query row / TMEM lane) read the accumulators with tcgen05.ld and filter.
+// Two shared-memory stages for series tiles, two TMEM accumulators.  Every
+// mbarrier wait is bounded; on a timeout the CTA raises an error flag,
+// drains, frees its tensor memory and stops.
+#include <cuda_bf16.h>
+
+#include "hk_device.cuh"
+#include "hk_internal.cuh"
+
+namespace hk {
+namespace {
+
+constexpr int kTcM = 128;        // queries per block (MMA M)
+constexpr int kTcN = 128;        // series per tile (MMA N)
+constexpr int kTcStages = 2;
+constexpr int kTcThreads = 192;  // 6 warps
+constexpr int kTmemCols = 256;   // two accumulators of kTcN columns
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far above any legitimate wait
+constexpr int kLocalK = 32;      // k up to this tightens U per row
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase with the given parity to complete: gives up
+// after kWaitNs of wall time or when the CTA is aborting (then returns
+// false; on its own timeout it sets the abort flag).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if ((it & 255) == 0 && global_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+// The same, decided once for a whole warp (every lane polls, all agree).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        const bool ok = mbar_try(bar, parity);
+        if (__all_sync(0xffffffffu, ok)) return true;
+        const bool stop = *abort_flag != 0;
+        if (__any_sync(0xffffffffu, stop)) return false;
+        if ((it & 255) == 255) {
+            const bool late = global_ns() - t0 > kWaitNs;
+            if (__any_sync(0xffffffffu, late)) {
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+// Shared memory matrix descriptor: no swizzle, K-major.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+    return d;                 // base offset 0, swizzle none
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcShared {
+    uint64_t full[kTcStages];
+    uint64_t empty[kTcStages];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint32_t tmem_base;
+    int abort_flag;
+    int64_t item;
+    int64_t s0, s1, base;
+    int tiles, gq, leaf;
+    int qid[kTcM];
+};
+
+}  // namespace
+
+// One CTA per SM; loops over (leaf, query block, series range) items.
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    const int n = A.n;
+    const uint32_t a_bytes = (uint32_t)kTcM * n * 2;
+    const uint32_t b_bytes = (uint32_t)kTcN * n * 2;
+    unsigned char *sA = tc_smem;                             // 1024-aligned
+    unsigned char *sB = tc_smem + a_bytes;                   // stages follow
+    float *kbest = reinterpret_cast<float *>(sB + kTcStages * b_bytes);   // kTcM * kLocalK
+    TcShared &S = *reinterpret_cast<TcShared *>(kbest + kTcM * kLocalK);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S.acc_full[b], 1);
+            mbar_init(&S.acc_empty[b], kTcM);
+        }
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {   // the MMA warp owns the tensor memory
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const int64_t total = A.item_off[A.L];
+    const int ksteps = n / 16;
+    const uint32_t lbo = 128, sbo = (uint32_t)(n / 8) * 128;
+
+    // running counts of barrier completions (phases), kept per role
+    uint32_t g_tile = 0;   // tiles processed by this CTA so far (all roles agree)
+    long long my_cand = 0, my_pairs = 0;
+
+    for (;;) {
+        if (tid == 0) S.item = atomicAdd(A.work_ctr, 1);
+        __syncthreads();
+        const int64_t it = S.item;
+        if (it >= total || S.abort_flag) break;
+        if (tid == 0) {
+            const int leaf = find_segment<int64_t>(A.item_off, (int)A.L + 1, it);
+            const int64_t local = it - A.item_off[leaf];
+            const int nql = A.leaf_qoff[leaf + 1] - A.leaf_qoff[leaf];
+            const int ngroups = (nql + kTcM - 1) / kTcM;
+            const int64_t tile = local / ngroups;
+            const int grp = (int)(local % ngroups);
+            const int64_t lo = A.leaf_off[leaf], hi = A.leaf_off[leaf + 1];
+            S.s0 = lo + tile * A.S_T;
+            S.s1 = min(S.s0 + (int64_t)A.S_T, hi);
+            S.base = S.s0 & ~(int64_t)7;
+            S.tiles = (int)((S.s1 - S.base + kTcN - 1) / kTcN);
+            S.gq = min(kTcM, nql - grp * kTcM);
+            S.leaf = leaf;
+            const int32_t *lq = A.leaf_q + A.leaf_qoff[leaf] + grp * kTcM;
+            for (int g = 0; g < kTcM; ++g) S.qid[g] = g < S.gq ? lq[g] : -1;
+        }
+        __syncthreads();
+        // gather the query block into the core-matrix layout (zeros past gq)
+        {
+            const int chunks = kTcM * (n / 8);   // 16-byte pieces
+            for (int c = tid; c < chunks; c += kTcThreads) {
+                const int r = c / (n / 8), k8 = c % (n / 8);
+                uint4 v = make_uint4(0, 0, 0, 0);
+                const int q = S.qid[r];
+                if (q >= 0) v = *reinterpret_cast<const uint4 *>(A.Qb + (int64_t)q * n + k8 * 8);
+                *reinterpret_cast<uint4 *>(sA + ((r >> 3) * (n / 8) + k8) * 128 + (r & 7) * 16) = v;
+            }
+            fence_proxy_async();
+        }
+        __syncthreads();
+        const int T = S.tiles;
+        const int64_t base = S.base, s0 = S.s0, s1 = S.s1;
+
+        if (warp == 0) {
+            // ---------------- producer: one bulk copy per tile
+            if (lane == 0) {
+                for (int t = 0; t < T; ++t) {
+                    const uint32_t gt = g_tile + t;
+                    const int s = gt % kTcStages;
+                    const uint32_t use = gt / kTcStages;
+                    if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1, &S.abort_flag)) break;
+                    const int64_t row0 = base + (int64_t)t * kTcN;
+                    mbar_arrive_expect_tx(&S.full[s], b_bytes);
+                    bulk_g2s(sB + s * b_bytes, A.Xb + row0 * n, b_bytes, &S.full[s]);
+                }
+            }
+        } else if (warp == 1) {
+            // ---------------- MMA issuer
+            if (lane == 0) {
+                const uint32_t a_base = smem_u32(sA);
+                for (int t = 0; t < T; ++t) {
+                    const uint32_t gt = g_tile + t;
+                    const int s = gt % kTcStages;
+                    const uint32_t use = gt / kTcStages;
+                    const int b = gt & 1;
+                    const uint32_t ause = gt >> 1;
+                    if (ause > 0 && !mbar_wait(&S.acc_empty[b], (ause - 1) & 1, &S.abort_flag)) break;
+                    if (!mbar_wait(&S.full[s], use & 1, &S.abort_flag)) break;
+                    tc_fence_after();
+                    const uint32_t b_base = smem_u32(sB + s * b_bytes);
+                    const uint32_t d = tmem + (uint32_t)(b * kTcN);
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t ad = smem_desc(a_base + ks * 2 * 128, lbo, sbo);
+                        const uint64_t bd = smem_desc(b_base + ks * 2 * 128, lbo, sbo);
+                        mma_bf16(d, ad, bd, A.idesc, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&S.empty[s]);
+                    mma_commit(&S.acc_full[b]);
+                }
+            }
+        } else {
+            // ---------------- epilogue: thread r owns query row r
+            const int r = (warp & 3) * 32 + lane;   // TMEM lane quarter of this warp
+            const int q = S.qid[r];
+            float q2 = 0.f, qa = 0.f, U = 0.f;
+            if (q >= 0) {
+                q2 = A.q2[q];
+                qa = A.qa[q];
+                U = __uint_as_float(A.U[q]);
+            }
+            float *kb = kbest + r * kLocalK;
+            const int kl = A.k <= kLocalK ? A.k : 0;
+            for (int i = 0; i < kl; ++i) kb[i] = INFINITY;
+            float kth = INFINITY;      // k-th smallest D~ + E seen by this row
+            for (int t = 0; t < T; ++t) {
+                const uint32_t gt = g_tile + t;
+                const int b = gt & 1;
+                const uint32_t ause = gt >> 1;
+                if (!mbar_wait_warp(&S.acc_full[b], ause & 1, &S.abort_flag)) break;
+                tc_fence_after();
+                if (q >= 0) U = fminf(U, __uint_as_float(A.U[q]));
+                const int64_t row0 = base + (int64_t)t * kTcN;
+                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * kTcN);
+                for (int c0 = 0; c0 < kTcN; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    if (q < 0) continue;
+#pragma unroll 4
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t pos = row0 + c0 + j;
+                        if (pos < s0 || pos >= s1) continue;
+                        const float x2 = __ldg(A.x2 + pos), xn = __ldg(A.xn + pos);
+                        const float qx = q2 + x2;
+                        const float dt = fmaf(-2.0f, v[j], qx);
+                        const float e = fmaf(qa, xn, A.eb * qx);
+                        const float lo = dt - e;
+                        ++my_pairs;
+                        if (A.dbg) A.dbg[(int64_t)q * A.N + pos] = dt;
+                        if (lo <= U) {
+                            const float up = dt + e;
+                            if (kl && up < kth) {
+                                // replace the largest of the row's k best
+                                int m = 0;
+                                for (int i = 1; i < kl; ++i) if (kb[i] > kb[m]) m = i;
+                                kb[m] = up;
+                                float mx = kb[0];
+                                for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i]);
+                                kth = mx;
+                                U = fminf(U, kth);
+                            }
+                            if (lo <= U) {
+                                const int slot = atomicAdd(&A.cand_cnt[q], 1);
+                                if (slot < A.cand_C) {
+                                    A.cand_p[(int64_t)q * A.cand_C + slot] = (int32_t)pos;
+                                    A.cand_lb[(int64_t)q * A.cand_C + slot] = lo;
+                                    ++my_cand;
+                                } else {
+                                    atomicOr(&A.qflag[q], 1);
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&S.acc_empty[b]);
+                if (q >= 0 && kth < INFINITY) atomicMin(&A.U[q], __float_as_uint(kth));
+            }
+        }
+        g_tile += T;
+        __syncthreads();
+    }
+    // drain: a CTA that aborted may have copies or MMAs in flight; wait for
+    // the last tile's barriers (bounded), then free the tensor memory.
+    if (S.abort_flag) {
+        if (tid == 0) atomicOr(A.err, 2);
+        if (tid == 0 && g_tile > 0) {
+            // let in-flight bulk copies land before the CTA's memory goes away
+            const uint64_t t0 = global_ns();
+            while (global_ns() - t0 < 100000000ull) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    }
+    my_pairs = warp_sum_ll(my_pairs);
+    my_cand = warp_sum_ll(my_cand);
+    if (lane == 0 && A.stats) {
+        stat_add(&A.stats[A.stat_pairs], my_pairs);
+        stat_add(&A.stats[A.stat_cands], my_cand);
+    }
+}
+
+// BF16 copy of the leaf-ordered collection in core-matrix order, and the
+// squared norms (binary64 sums of the float32 rows, rounded up) and norms.
+__global__ void k_make_bf16(const float *__restrict__ X, int64_t N, int n, int64_t Npad,
+                            __nv_bfloat16 *__restrict__ Xb, float *__restrict__ x2,
+                            float *__restrict__ xn) {
+    const int nk = n / 8;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Npad * nk;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = c / nk;
+        const int k8 = (int)(c % nk);
+        __nv_bfloat16 h[8];
+        if (i < N) {
+            const float4 a = *reinterpret_cast<const float4 *>(X + i * n + k8 * 8);
+            const float4 b = *reinterpret_cast<const float4 *>(X + i * n + k8 * 8 + 4);
+            h[0] = __float2bfloat16_rn(a.x); h[1] = __float2bfloat16_rn(a.y);
+            h[2] = __float2bfloat16_rn(a.z); h[3] = __float2bfloat16_rn(a.w);
+            h[4] = __float2bfloat16_rn(b.x); h[5] = __float2bfloat16_rn(b.y);
+            h[6] = __float2bfloat16_rn(b.z); h[7] = __float2bfloat16_rn(b.w);
+        } else {
+            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(0.0f);
+        }
+        const int64_t off = (((i >> 3) * nk + k8) * 8 + (i & 7)) * 8;
+        *reinterpret_cast<uint4 *>(Xb + off) = *reinterpret_cast<const uint4 *>(h);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Npad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        if (i < N)
+            for (int j = 0; j < n; ++j) s += (double)X[i * n + j] * (double)X[i * n + j];
+        x2[i] = __double2float_ru(s);
+        xn[i] = __double2float_ru(sqrt(s));
+    }
+}
+
+// Queries: bfloat16 rows, squared norms and the per-query error coefficient.
+__global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, float c_rel,
+                           __nv_bfloat16 *__restrict__ Qb, float *__restrict__ q2,
+                           float *__restrict__ qa) {
+    const int q = blockIdx.x;
+    if (q >= nq) return;
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const float v = Q[(int64_t)q * n + j];
+        Qb[(int64_t)q * n + j] = __float2bfloat16_rn(v);
+        s += (double)v * (double)v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        q2[q] = __double2float_ru(t);
+        qa[q] = __double2float_ru(c_rel * sqrt(t));
+    }
+}
+
+// Exact float32 distances of the candidates at or below the final bound into
+// the query's pool (warp per candidate).
+__global__ void k_tc_rescore(const float *__restrict__ Q, const float *__restrict__ X, int n,
+                             const int32_t *__restrict__ cand_cnt, const int32_t *__restrict__ cand_p,
+                             const float *__restrict__ cand_lb, int cand_C,
+                             const uint32_t *__restrict__ U, float *__restrict__ pool_d,
+                             int32_t *__restrict__ pool_p, int32_t *__restrict__ pool_cnt, int pool_C,
+                             int32_t *__restrict__ qflag, long long *__restrict__ stats, int stat_slot) {
+    const int q = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int cnt = min(cand_cnt[q], cand_C);
+    const float u = __uint_as_float(U[q]);
+    const int wpb = blockDim.x >> 5;
+    long long done = 0;
+    for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < cnt; c += gridDim.x * wpb) {
+        if (cand_lb[(int64_t)q * cand_C + c] > u) continue;
+        const int32_t pos = cand_p[(int64_t)q * cand_C + c];
+        const float *x = X + (int64_t)pos * n;
+        const float *qq = Q + (int64_t)q * n;
+        float a = 0.0f;
+        for (int j = lane; j < n; j += 32) {
+            const float d = qq[j] - x[j];
+            a = fmaf(d, d, a);
+        }
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) {
+            ++done;
+            const int slot = atomicAdd(&pool_cnt[q], 1);
+            if (slot < pool_C) {
+                pool_d[(int64_t)q * pool_C + slot] = a;
+                pool_p[(int64_t)q * pool_C + slot] = pos;
+            } else {
+                atomicOr(&qflag[q], 1);
+            }
+        }
+    }
+    if (lane == 0 && done) stat_add(&stats[stat_slot], done);
+}
+
+size_t tc_smem_bytes(int n) {
+    return (size_t)kTcM * n * 2 + (size_t)kTcStages * kTcN * n * 2 + (size_t)kTcM * kLocalK * 4 +
+           sizeof(TcShared) + 1024;
+}
+
+uint32_t tc_idesc() {
+    uint32_t d = 0;
+    d |= 1u << 4;                          // D format: float32
+    d |= 1u << 7;                          // A format: bfloat16
+    d |= 1u << 10;                         // B format: bfloat16
+    d |= (uint32_t)(kTcN >> 3) << 17;      // N
+    d |= (uint32_t)(kTcM >> 4) << 24;      // M
+    return d;                              // both operands K-major, dense
+}
+
+double tc_error_coefficient(int n) {
+    const double u = std::ldexp(1.0, -8);
+    const double w = std::ldexp(1.0, -20);
+    const double g = n * w / (1.0 - n * w);
+    const double c1 = 2 * u + u * u + g * (1 + u) * (1 + u);
+    return (2.0 * c1 + std::ldexp(1.0, -18)) * (1.0 + std::ldexp(1.0, -10));
+}
+
+void launch_tc_scan(const TcArgs &a, cudaStream_t s) {
+    const size_t smem = tc_smem_bytes(a.n);
+    static bool configured = false;
+    if (!configured) {
+        HK_CHECK_CUDA(cudaFuncSetAttribute(k_tc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)tc_smem_bytes(256)));
+        configured = true;
+    }
+    int dev = 0, sms = 0;
+    HK_CHECK_CUDA(cudaGetDevice(&dev));
+    HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    k_tc_scan<<<sms, kTcThreads, smem, s>>>(a);
+    HK_CHECK_LAUNCH();
+}
+
+void launch_make_bf16(const float *X, int64_t N, int n, int64_t Npad, void *Xb, float *x2, float *xn,
+                      cudaStream_t s) {
+    int dev = 0, sms = 0;
+    HK_CHECK_CUDA(cudaGetDevice(&dev));
+    HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    k_make_bf16<<<sms * 16, 256, 0, s>>>(X, N, n, Npad, reinterpret_cast<__nv_bfloat16 *>(Xb), x2, xn);
+    HK_CHECK_LAUNCH();
+}
+
+void launch_tc_qprep(const float *Q, int nq, int n, double c_rel, void *Qb, float *q2, float *qa,
+                     cudaStream_t s) {
+    k_tc_qprep<<<nq, 128, 0, s>>>(Q, nq, n, (float)c_rel, reinterpret_cast<__nv_bfloat16 *>(Qb), q2, qa);
+    HK_CHECK_LAUNCH();
+}
+
+void launch_tc_rescore(const float *Q, const float *X, int n, int nq, const int32_t *cand_cnt,
+                       const int32_t *cand_p, const float *cand_lb, int cand_C, const uint32_t *U,
+                       float *pool_d, int32_t *pool_p, int32_t *pool_cnt, int pool_C, int32_t *qflag,
+                       long long *stats, int stat_slot, cudaStream_t s) {
+    dim3 grid(8, (unsigned)nq);
+    k_tc_rescore<<<grid, 256, 0, s>>>(Q, X, n, cand_cnt, cand_p, cand_lb, cand_C, U, pool_d, pool_p,
+                                      pool_cnt, pool_C, qflag, stats, stat_slot);
+    HK_CHECK_LAUNCH();
+}
+
+}  // namespace hk

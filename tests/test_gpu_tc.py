@@ -1,0 +1,89 @@
+"""Precision form: tensor-core distances with a certified bound.
+
+The bound is pinned pair by pair: for every query and series, the
+tensor-core value D~ = |q|^2 + |x|^2 - 2 q^.x^ must lie within E of the exact
+squared distance (binary64 from numpy, a separate implementation), so the
+candidate filter never drops a true neighbour.  Answers through the
+precision form must equal the brute-force oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hb():
+    from paper_2212_13297_gb300 import build, binding
+    build.build()
+    binding.lib()
+    assert torch.cuda.is_available(), "GPU test without a GPU"
+    return binding
+
+
+def _wl():
+    from paper_2212_13297_gb300 import workload
+    return workload
+
+
+@pytest.mark.parametrize("N,n,kind", [(3000, 256, "rw"), (2500, 64, "rw"), (2000, 96, "gauss"),
+                                      (1800, 128, "rw")])
+def test_tc_distance_within_certified_bound(hb, N, n, kind):
+    wl = _wl()
+    X = wl.random_walk(N, n, seed=N, device="cuda") if kind == "rw" else \
+        wl.gaussian(N, n, seed=N, device="cuda")
+    Q, _ = wl.queries(X, 9, [0.01, 0.5, 1.0], seed=3, norm="z" if kind == "rw" else None)
+    idx = hb.Index(X, 100, flags=hb.HK_BUILD_BF16)
+    assert idx.info()["has_bf16"] == 1
+    ex = idx.export()
+    dt, err = idx.debug_tc_dist(Q)
+    Xl = X.cpu().numpy().astype(np.float64)[ex["perm"]]
+    Qh = Q.cpu().numpy().astype(np.float64)
+    exact = ((Qh[:, None, :] - Xl[None, :, :]) ** 2).sum(-1)
+    assert np.isfinite(dt).all(), "some pairs were not computed"
+    dev = np.abs(dt.astype(np.float64) - exact)
+    assert (dev <= err).all(), float((dev / err).max())
+    # the bound is not vacuous: bfloat16 rounding shows up at a visible
+    # fraction of it, and it stays small next to typical distances
+    assert 0.01 < float(np.median(dev / err)) < 0.5
+    assert float(np.median(err / exact)) < 0.05
+
+
+@pytest.mark.parametrize("N,n,tau,nq,k,sig", [
+    (20000, 256, 300, 20, 10, [0.5, 1.0]),
+    (20000, 256, 300, 150, 1, [0.3, 1.0]),
+    (15000, 64, 200, 30, 50, [0.1, 1.0]),
+    (12000, 96, 150, 16, 5, [0.5]),
+])
+def test_tc_query_matches_bruteforce(hb, oracle_lib, N, n, tau, nq, k, sig):
+    wl = _wl()
+    X = wl.random_walk(N, n, seed=N + n, device="cuda")
+    Q, _ = wl.queries(X, nq, sig, seed=k)
+    idx = hb.Index(X, tau, flags=hb.HK_BUILD_BF16)
+    ids, dist, st = idx.query(Q, k, flags=hb.HK_Q_BF16)
+    oids, od2 = oracle.knn(X.cpu().numpy(), Q.cpu().numpy(), k)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    np.testing.assert_allclose(dist.cpu().numpy(), np.sqrt(od2).astype(np.float32), rtol=1e-5)
+    assert st["tc_pairs"] > 0
+    # the plain path gives the same answer
+    ids2, _, _ = idx.query(Q, k)
+    np.testing.assert_array_equal(ids2.cpu().numpy(), oids)
+
+
+def test_tc_ties_and_flag_checks(hb, oracle_lib):
+    wl = _wl()
+    X = wl.random_walk(6000, 128, seed=8, device="cuda")
+    X[3000:3040] = X[9]
+    Q = torch.cat([X[[9]], wl.queries(X, 3, 0.7, seed=2)[0]]).contiguous()
+    idx = hb.Index(X, 100, flags=hb.HK_BUILD_BF16)
+    ids, dist, _ = idx.query(Q, 20, flags=hb.HK_Q_BF16)
+    oids, _ = oracle.knn(X.cpu().numpy(), Q.cpu().numpy(), 20)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    plain = hb.Index(X, 100)
+    with pytest.raises(hb.HerculesError) as e:
+        plain.query(Q, 5, flags=hb.HK_Q_BF16)
+    assert e.value.code == hb.HK_EINVAL
