@@ -224,12 +224,13 @@ int hk_debug_lb_eapca(hk_index *idx, const float *Q, int32_t nq, double *out);
 int hk_debug_lb_sax(hk_index *idx, const float *Q, int32_t nq, float *out);
 
 /*
- * hk_debug_tc_dist -- the tensor-core form's D~(q, x) = |q|^2 + |x|^2 - 2 q^.x^
- * (bfloat16 operands, float32 accumulation) for every query and every series
- * in leaf order, dt[q*N + pos], and the certified bound E(q, x) the filter
- * uses, err[q*N + pos] (index built with HK_BUILD_BF16).  Host outputs.
+ * hk_debug_tc_dist -- the certified interval [lo, up] that the tensor-core
+ * form puts around the squared distance of every query and every series in
+ * leaf order, lo[q*N + pos], up[q*N + pos] (index built with HK_BUILD_BF16):
+ * D~ = |q|^2 + |x|^2 - 2 q^.x^ (bfloat16 operands, float32 accumulation)
+ * minus / plus its error bound.  Host outputs.
  */
-int hk_debug_tc_dist(hk_index *idx, const float *Q, int32_t nq, float *dt, float *err);
+int hk_debug_tc_dist(hk_index *idx, const float *Q, int32_t nq, float *lo, float *up);
 
 const char *hk_last_error(void);
 const char *hk_version(void);

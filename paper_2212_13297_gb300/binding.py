@@ -223,11 +223,12 @@ class Index:
         return out
 
     def debug_tc_dist(self, Q):
-        """(D~ [nq, N], E [nq, N]) from the tensor-core kernel, leaf order."""
-        dt = np.empty((Q.shape[0], self.N), np.float32)
-        err = np.empty((Q.shape[0], self.N), np.float32)
-        _check(lib().hk_debug_tc_dist(self._h, _ptr(Q), Q.shape[0], _ptr(dt), _ptr(err)))
-        return dt, err
+        """Certified interval (lo [nq, N], up [nq, N]) of the tensor-core
+        form around every squared distance, leaf order."""
+        lo = np.empty((Q.shape[0], self.N), np.float32)
+        up = np.empty((Q.shape[0], self.N), np.float32)
+        _check(lib().hk_debug_tc_dist(self._h, _ptr(Q), Q.shape[0], _ptr(lo), _ptr(up)))
+        return lo, up
 
     def debug_lb_sax(self, Q):
         out = np.empty((Q.shape[0], self.N), np.float32)

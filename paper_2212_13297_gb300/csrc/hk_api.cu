@@ -113,7 +113,7 @@ int hk_index_info_get(const hk_index *idx, hk_index_info *out) {
                                       idx->leaf_seg.bytes() + idx->env.bytes() +
                                       idx->seg_ab.bytes() + idx->bp.bytes());
         out->has_bf16 = idx->has_bf16 ? 1 : 0;
-        out->device_bytes += (int64_t)(idx->Xb.bytes() + idx->x2.bytes() + idx->xn.bytes());
+        out->device_bytes += (int64_t)(idx->Xb.bytes() + idx->xq.bytes());
     });
 }
 
@@ -203,14 +203,14 @@ int hk_debug_lb_sax(hk_index *idx, const float *Q, int32_t nq, float *out) {
     });
 }
 
-int hk_debug_tc_dist(hk_index *idx, const float *Q, int32_t nq, float *dt, float *err) {
+int hk_debug_tc_dist(hk_index *idx, const float *Q, int32_t nq, float *lo, float *up) {
     return guard([&] {
-        if (!idx || !Q || !dt || !err || nq < 1) hk::fail(HK_EINVAL, "bad argument");
+        if (!idx || !Q || !lo || !up || nq < 1) hk::fail(HK_EINVAL, "bad argument");
         if (!idx->has_bf16) hk::fail(HK_EINVAL, "index built without HK_BUILD_BF16");
         if (idx->n > hk::kTcMaxLen) hk::fail(HK_EINVAL, "n=%d > %d", idx->n, hk::kTcMaxLen);
         hk::DevBuf<float> tmp;
         const float *Qd = device_view(Q, (size_t)nq * idx->n, idx->stream, tmp);
-        hk::debug_tc_dist(idx, Qd, nq, dt, err);
+        hk::debug_tc_dist(idx, Qd, nq, lo, up);
     });
 }
 

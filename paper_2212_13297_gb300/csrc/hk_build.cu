@@ -663,9 +663,8 @@ void build_index(hk_index *idx, const float *Xsrc, int64_t N, int n, const hk_bu
         // tile starting at any 8-aligned position stays inside the buffer
         idx->Npad = ((N + 7) / 8) * 8 + 136;
         idx->Xb.alloc((size_t)idx->Npad * n, s);
-        idx->x2.alloc(idx->Npad, s);
-        idx->xn.alloc(idx->Npad, s);
-        launch_make_bf16(idx->X.p, N, n, idx->Npad, idx->Xb.p, idx->x2.p, idx->xn.p, s);
+        idx->xq.alloc(idx->Npad, s);
+        launch_make_bf16(idx->X.p, N, n, idx->Npad, idx->Xb.p, idx->xq.p, s);
         idx->has_bf16 = true;
     }
     HK_CHECK_CUDA(cudaStreamSynchronize(s));

@@ -119,7 +119,7 @@ struct Workspace {
     DevBuf<float> out_dist;     // nq * k
     DevBuf<int32_t> approx;     // nq * A
     DevBuf<uint16_t> Qb;        // bfloat16 queries (tensor-core form)
-    DevBuf<float> q2, qa;       // query squared norms, error coefficients
+    DevBuf<float> q2, qa;       // query |q|^2 (1-eb) rounded down, error coefficients
     DevBuf<int32_t> cand_cnt;   // nq    tensor-core candidates per query
     DevBuf<int32_t> cand_p;     // nq * cand_C
     DevBuf<float> cand_lb;      // nq * cand_C  lower bound D~ - E
@@ -163,7 +163,7 @@ struct hk_index {
     hk::DevBuf<int32_t> seg_ab;    // S*2  (a, b)
     hk::DevBuf<float> bp;          // 255 breakpoints
     hk::DevBuf<uint16_t> Xb;       // bfloat16 copy in core-matrix order (HK_BUILD_BF16)
-    hk::DevBuf<float> x2, xn;      // squared norms and norms of the float32 rows
+    hk::DevBuf<float2> xq;         // {|x|^2 (1-eb) rounded down, |x| rounded up} per series
     int64_t Npad = 0;
     bool has_bf16 = false;
 
@@ -187,7 +187,7 @@ void run_scan(const float *Xdev, int64_t N, int n, const float *Qdev, int nq, in
               cudaStream_t s, int64_t *out_ids, float *out_dist);
 void debug_lb_eapca(hk_index *idx, const float *Qdev, int nq, double *out_host);
 void debug_lb_sax(hk_index *idx, const float *Qdev, int nq, float *out_host);
-void debug_tc_dist(hk_index *idx, const float *Qdev, int nq, float *dt_host, float *err_host);
+void debug_tc_dist(hk_index *idx, const float *Qdev, int nq, float *lo_host, float *up_host);
 void check_finite(const float *p, int64_t count, cudaStream_t s, const char *what);
 void check_finite_with(const float *p, int64_t count, cudaStream_t s, const char *what,
                        unsigned long long *dev_counter);
@@ -219,11 +219,11 @@ struct ScanScratch {
 // Arguments of the tensor-core distance scan (hk_tc.cu).
 struct TcArgs {
     const uint16_t *Xb;          // bfloat16 collection, core-matrix order, padded rows
-    const float *x2, *xn;        // per position: squared norm, norm (rounded up)
+    const float2 *xq;            // per position: {|x|^2 (1-eb) rounded down, |x| rounded up}
     int n;
     const uint16_t *Qb;          // bfloat16 queries, row-major
-    const float *q2, *qa;        // per query: squared norm, error coefficient * norm
-    float eb;                    // relative error coefficient on |q|^2 + |x|^2
+    const float *q2e, *qa;       // per query: |q|^2 (1-eb) rounded down, c |q| rounded up
+    float eb2;                   // 2 eb / (1 - eb) with margin: the upper bound's norm term
     const int64_t *leaf_off;
     int64_t L;
     const int32_t *leaf_qoff, *leaf_q;
@@ -240,13 +240,13 @@ struct TcArgs {
     long long *stats;
     int stat_pairs, stat_cands;
     uint32_t idesc;
-    float *dbg;                  // if set: D~ of every pair, dbg[q * N + pos]
+    float *dbg_lo, *dbg_up;      // if set: certified interval of every pair, [q * N + pos]
     int64_t N;
 };
 void launch_tc_scan(const TcArgs &a, cudaStream_t s);
-void launch_make_bf16(const float *X, int64_t N, int n, int64_t Npad, void *Xb, float *x2, float *xn,
+void launch_make_bf16(const float *X, int64_t N, int n, int64_t Npad, void *Xb, void *xq,
                       cudaStream_t s);
-void launch_tc_qprep(const float *Q, int nq, int n, double c_rel, void *Qb, float *q2, float *qa,
+void launch_tc_qprep(const float *Q, int nq, int n, double c_rel, void *Qb, float *q2e, float *qa,
                      cudaStream_t s);
 void launch_tc_rescore(const float *Q, const float *X, int n, int nq, const int32_t *cand_cnt,
                        const int32_t *cand_p, const float *cand_lb, int cand_C, const uint32_t *U,
@@ -255,6 +255,7 @@ void launch_tc_rescore(const float *Q, const float *X, int n, int nq, const int3
 size_t tc_smem_bytes(int n);
 uint32_t tc_idesc();
 double tc_error_coefficient(int n);
+float tc_eb2();
 constexpr int kTcMaxLen = 256;     // longest series the tensor-core form takes
 
 // Exhaustive exact k-NN into caller device buffers using only `sc`.

@@ -1035,7 +1035,9 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     const float eapca_th = o.eapca_th >= 0 ? o.eapca_th : 0.25f;
     ScanConfig cfg = choose_scan(n, k, !nosax, o.query_group);
     const int S_T = o.series_tile > 0 ? o.series_tile : 8192;
-    const int pool_C = std::min(65536, std::max(4096, 64 * cfg.cap));
+    // the precision form's bound admits a band of near candidates around the
+    // k-th distance (a few thousand on hard queries): give its pool room
+    const int pool_C = tc ? std::max(65536, 256 * k) : std::min(65536, std::max(4096, 64 * cfg.cap));
 
     reserve_common(ws, nq, L, k, pool_C, s);
     ws.qseg.reserve((size_t)nq * idx->S * 2, s);
@@ -1138,7 +1140,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     if (tc) {
         // a9: tensor-core distances with a certified bound, then the exact
         // float32 rescore of the survivors into the pool
-        const int cand_C = std::max(4096, 256 * k);
+        const int cand_C = std::max(65536, 256 * k);
         ws.cand_cnt.reserve(nq, s);
         ws.cand_p.reserve((size_t)nq * cand_C, s);
         ws.cand_lb.reserve((size_t)nq * cand_C, s);
@@ -1148,13 +1150,12 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         build_lists(ws, v, 128, S_tc, 2, nq, s);
         TcArgs t{};
         t.Xb = idx->Xb.p;
-        t.x2 = idx->x2.p;
-        t.xn = idx->xn.p;
+        t.xq = idx->xq.p;
         t.n = n;
         t.Qb = ws.Qb.p;
-        t.q2 = ws.q2.p;
+        t.q2e = ws.q2.p;
         t.qa = ws.qa.p;
-        t.eb = (float)(std::ldexp(1.0, -19) * (1.0 + std::ldexp(1.0, -10)));
+        t.eb2 = tc_eb2();
         t.leaf_off = v.leaf_off;
         t.L = L;
         t.leaf_qoff = ws.leaf_qoff.p;
@@ -1174,7 +1175,8 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         t.stat_pairs = ST_TC_PAIRS;
         t.stat_cands = ST_TC_CANDS;
         t.idesc = tc_idesc();
-        t.dbg = nullptr;
+        t.dbg_lo = nullptr;
+        t.dbg_up = nullptr;
         t.N = idx->N;
         if (timer) timer->mark(s);
         launch_tc_scan(t, s);
@@ -1226,7 +1228,11 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
         HK_CHECK_LAUNCH();
         std::vector<int32_t> flags2;
         std::vector<uint32_t> U2;
-        query_pass(idx, w2, w2.Q.p, nsub, k, o, s, w2.Uinit.p, &timer, flags2, U2);
+        // the retry takes the float32 path: its bound is ~1e-5 relative, so
+        // near-ties that crowd the precision form's wider band fit its lists
+        hk_query_opts o2 = o;
+        o2.flags &= ~HK_Q_BF16;
+        query_pass(idx, w2, w2.Q.p, nsub, k, o2, s, w2.Uinit.p, &timer, flags2, U2);
         LeafView v;
         v.X = idx->X.p;
         v.perm = idx->perm.p;
@@ -1410,9 +1416,9 @@ void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
 }
 
-// D~ for every (query, series) pair from the tensor-core kernel, and the
-// certified bound E that the filter uses, for tests of the bound.
-void debug_tc_dist(hk_index *idx, const float *Qd, int nq, float *dt_host, float *err_host) {
+// The certified interval [lo, up] of every (query, series) pair as the
+// tensor-core kernel forms it, for tests of the bound.
+void debug_tc_dist(hk_index *idx, const float *Qd, int nq, float *lo_host, float *up_host) {
     cudaStream_t s = idx->stream;
     Workspace ws;
     const int n = idx->n;
@@ -1437,18 +1443,19 @@ void debug_tc_dist(hk_index *idx, const float *Qd, int nq, float *dt_host, float
     ws.cand_p.reserve((size_t)nq * cand_C, s);
     ws.cand_lb.reserve((size_t)nq * cand_C, s);
     HK_CHECK_CUDA(cudaMemsetAsync(ws.cand_cnt.p, 0, nq * sizeof(int32_t), s));
-    DevBuf<float> dbg;
-    dbg.alloc((size_t)nq * N, s);
-    HK_CHECK_CUDA(cudaMemsetAsync(dbg.p, 0xff, (size_t)nq * N * sizeof(float), s));   // NaN
+    DevBuf<float> dlo, dup;
+    dlo.alloc((size_t)nq * N, s);
+    dup.alloc((size_t)nq * N, s);
+    HK_CHECK_CUDA(cudaMemsetAsync(dlo.p, 0xff, (size_t)nq * N * sizeof(float), s));   // NaN
+    HK_CHECK_CUDA(cudaMemsetAsync(dup.p, 0xff, (size_t)nq * N * sizeof(float), s));
     TcArgs t{};
     t.Xb = idx->Xb.p;
-    t.x2 = idx->x2.p;
-    t.xn = idx->xn.p;
+    t.xq = idx->xq.p;
     t.n = n;
     t.Qb = ws.Qb.p;
-    t.q2 = ws.q2.p;
+    t.q2e = ws.q2.p;
     t.qa = ws.qa.p;
-    t.eb = (float)(std::ldexp(1.0, -19) * (1.0 + std::ldexp(1.0, -10)));
+    t.eb2 = tc_eb2();
     t.leaf_off = v.leaf_off;
     t.L = L;
     t.leaf_qoff = ws.leaf_qoff.p;
@@ -1466,23 +1473,16 @@ void debug_tc_dist(hk_index *idx, const float *Qd, int nq, float *dt_host, float
     t.err = ws.counters.p + 2;
     t.stats = nullptr;
     t.idesc = tc_idesc();
-    t.dbg = dbg.p;
+    t.dbg_lo = dlo.p;
+    t.dbg_up = dup.p;
     t.N = N;
     launch_tc_scan(t, s);
     int32_t terr = 0;
     HK_CHECK_CUDA(cudaMemcpyAsync(&terr, ws.counters.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    HK_CHECK_CUDA(cudaMemcpyAsync(dt_host, dbg.p, (size_t)nq * N * sizeof(float), cudaMemcpyDeviceToHost, s));
-    // the bound: qa[q] * xn[pos] + eb * (q2[q] + x2[pos])
-    std::vector<float> q2(nq), qa(nq), x2(N), xn(N);
-    HK_CHECK_CUDA(cudaMemcpyAsync(q2.data(), ws.q2.p, nq * 4, cudaMemcpyDeviceToHost, s));
-    HK_CHECK_CUDA(cudaMemcpyAsync(qa.data(), ws.qa.p, nq * 4, cudaMemcpyDeviceToHost, s));
-    HK_CHECK_CUDA(cudaMemcpyAsync(x2.data(), idx->x2.p, N * 4, cudaMemcpyDeviceToHost, s));
-    HK_CHECK_CUDA(cudaMemcpyAsync(xn.data(), idx->xn.p, N * 4, cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(lo_host, dlo.p, (size_t)nq * N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaMemcpyAsync(up_host, dup.p, (size_t)nq * N * sizeof(float), cudaMemcpyDeviceToHost, s));
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
     if (terr) fail(HK_ETIMEOUT, "tensor-core scan: a bounded wait ran out (flag %d)", terr);
-    for (int q = 0; q < nq; ++q)
-        for (int64_t p = 0; p < N; ++p)
-            err_host[(int64_t)q * N + p] = qa[q] * xn[p] + t.eb * (q2[q] + x2[p]);
 }
 
 void debug_lb_eapca(hk_index *idx, const float *Qd, int nq, double *out_host) {

@@ -24,9 +24,13 @@
 // (next 8 points), stride-dimension offset (n/8)*128 bytes (next 8 series).
 // The query block is gathered into the same layout with ordinary stores.
 //
-// CTA roles (6 warps): warp 0 issues the bulk copies, warp 1 (one thread)
-// issues tcgen05.mma and tcgen05.commit, warps 2-5 (128 threads, one per
-// query row / TMEM lane) read the accumulators with tcgen05.ld and filter.
+// CTA roles (10 warps): warp 0 issues the bulk copies (series tile and the
+// tile's norm pairs), warp 1 (one thread) issues tcgen05.mma and
+// tcgen05.commit, warps 2-9 read the accumulators with tcgen05.ld and filter:
+// warp w reads TMEM lane quarter w%4 (query rows 32(w%4)..+31) and half of
+// the tile's columns.  Per element the filter is two FMAs and a compare
+// against a per-row threshold; the exact bounds are formed only for the
+// rare survivors.
 // Two shared-memory stages for series tiles, two TMEM accumulators.  Every
 // mbarrier wait is bounded; on a timeout the CTA raises an error flag,
 // drains, frees its tensor memory and stops.
@@ -41,10 +45,16 @@ namespace {
 constexpr int kTcM = 128;        // queries per block (MMA M)
 constexpr int kTcN = 128;        // series per tile (MMA N)
 constexpr int kTcStages = 2;
-constexpr int kTcThreads = 192;  // 6 warps
+// Norm slots: tile g uses slot g % 4.  The producer writes tile g's slot
+// only after the MMA of tile g-2 completed, which itself waited for the
+// epilogue of tile g-4, the slot's previous user.
+constexpr int kNormSlots = 4;
+constexpr int kTcEpiWarps = 8;   // two per TMEM lane quarter, each half the columns
+constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTmemCols = 256;   // two accumulators of kTcN columns
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far above any legitimate wait
-constexpr int kLocalK = 32;      // k up to this tightens U per row
+constexpr int kLocalK = 32;
+constexpr double kTcEb = 0x1p-19;   // relative term for norm and epilogue rounding      // 2k up to this tightens U per row
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -186,7 +196,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     const uint32_t b_bytes = (uint32_t)kTcN * n * 2;
     unsigned char *sA = tc_smem;                             // 1024-aligned
     unsigned char *sB = tc_smem + a_bytes;                   // stages follow
-    float *kbest = reinterpret_cast<float *>(sB + kTcStages * b_bytes);   // kTcM * kLocalK
+    float2 *sX = reinterpret_cast<float2 *>(sB + kTcStages * b_bytes);     // kNormSlots * kTcN
+    float *kbest = reinterpret_cast<float *>(sX + kNormSlots * kTcN);      // kTcM * kLocalK
     TcShared &S = *reinterpret_cast<TcShared *>(kbest + kTcM * kLocalK);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -197,7 +208,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&S.acc_full[b], 1);
-            mbar_init(&S.acc_empty[b], kTcM);
+            mbar_init(&S.acc_empty[b], 32 * kTcEpiWarps);
         }
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -269,8 +280,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                     const uint32_t use = gt / kTcStages;
                     if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1, &S.abort_flag)) break;
                     const int64_t row0 = base + (int64_t)t * kTcN;
-                    mbar_arrive_expect_tx(&S.full[s], b_bytes);
+                    mbar_arrive_expect_tx(&S.full[s], b_bytes + kTcN * (uint32_t)sizeof(float2));
                     bulk_g2s(sB + s * b_bytes, A.Xb + row0 * n, b_bytes, &S.full[s]);
+                    bulk_g2s(sX + (gt % kNormSlots) * kTcN, A.xq + row0, kTcN * (uint32_t)sizeof(float2),
+                             &S.full[s]);
                 }
             }
         } else if (warp == 1) {
@@ -298,72 +311,104 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                 }
             }
         } else {
-            // ---------------- epilogue: thread r owns query row r
+            // ---------------- epilogue: thread owns query row r, half the columns
             const int r = (warp & 3) * 32 + lane;   // TMEM lane quarter of this warp
+            const int half = (warp - 2) >> 2;       // column half
             const int q = S.qid[r];
-            float q2 = 0.f, qa = 0.f, U = 0.f;
+            float q2e = 0.f, qa = 0.f, U = 0.f;
             if (q >= 0) {
-                q2 = A.q2[q];
+                q2e = A.q2e[q];
                 qa = A.qa[q];
                 U = __uint_as_float(A.U[q]);
             }
             float *kb = kbest + r * kLocalK;
-            const int kl = A.k <= kLocalK ? A.k : 0;
+            // both halves of a row share its list; each keeps its own slots
+            const int kl = (A.k <= kLocalK / 2) ? A.k : 0;
+            kb += half * (kLocalK / 2);
             for (int i = 0; i < kl; ++i) kb[i] = INFINITY;
-            float kth = INFINITY;      // k-th smallest D~ + E seen by this row
+            float kth = INFINITY;      // k-th smallest upper bound seen by this thread
+            long long pairs = 0;
             for (int t = 0; t < T; ++t) {
                 const uint32_t gt = g_tile + t;
                 const int b = gt & 1;
+                const int s = gt % kTcStages;
                 const uint32_t ause = gt >> 1;
                 if (!mbar_wait_warp(&S.acc_full[b], ause & 1, &S.abort_flag)) break;
                 tc_fence_after();
                 if (q >= 0) U = fminf(U, __uint_as_float(A.U[q]));
                 const int64_t row0 = base + (int64_t)t * kTcN;
-                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * kTcN);
-                for (int c0 = 0; c0 < kTcN; c0 += 32) {
+                // columns of this tile inside [s0, s1)
+                const int jlo = (int)max((int64_t)0, s0 - row0);
+                const int jhi = (int)min((int64_t)kTcN, s1 - row0);
+                const float thr = U - q2e;   // lo <= U  <=>  x2e - qa|x| - 2v <= U - q2e
+                const float2 *xs = sX + (gt % kNormSlots) * kTcN;
+                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                       (uint32_t)(b * kTcN + half * (kTcN / 2));
+                for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
                     float v[32];
                     tmem_ld32(taddr + c0, v);
                     if (q < 0) continue;
-#pragma unroll 4
+                    const int cb = half * (kTcN / 2) + c0;
+                    // columns of this chunk inside [s0, s1)
+                    const int a = max(jlo - cb, 0), z = min(jhi - cb, 32);
+                    if (a >= z) continue;
+                    const uint32_t valid = (z >= 32 ? 0xffffffffu : ((1u << z) - 1u)) & ~((1u << a) - 1u);
+                    pairs += z - a;
+                    uint32_t hit = 0;
+#pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int64_t pos = row0 + c0 + j;
-                        if (pos < s0 || pos >= s1) continue;
-                        const float x2 = __ldg(A.x2 + pos), xn = __ldg(A.xn + pos);
-                        const float qx = q2 + x2;
-                        const float dt = fmaf(-2.0f, v[j], qx);
-                        const float e = fmaf(qa, xn, A.eb * qx);
-                        const float lo = dt - e;
-                        ++my_pairs;
-                        if (A.dbg) A.dbg[(int64_t)q * A.N + pos] = dt;
+                        const float2 xv = xs[cb + j];
+                        const float lhs = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x));
+                        hit |= (lhs <= thr ? 1u : 0u) << j;
+                    }
+                    hit &= valid;
+                    if (A.dbg_lo) {
+                        for (int j = a; j < z; ++j) {
+                            const float2 xv = xs[cb + j];
+                            const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
+                            const float bs = lo + 2.0f * qa * xv.y;
+                            A.dbg_lo[(int64_t)q * A.N + row0 + cb + j] = lo;
+                            A.dbg_up[(int64_t)q * A.N + row0 + cb + j] =
+                                bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x);
+                        }
+                    }
+                    while (hit) {
+                        // survivor: exact lower / upper bounds in the
+                        // certified form (rounded outward)
+                        const int j = __ffs(hit) - 1;
+                        hit &= hit - 1;
+                        const float2 xv = xs[cb + j];
+                        const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
+                        const float bs = lo + 2.0f * qa * xv.y;
+                        const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x);
+                        if (kl && up < kth) {
+                            int m = 0;
+                            for (int i = 1; i < kl; ++i) if (kb[i] > kb[m]) m = i;
+                            kb[m] = up;
+                            float mx = kb[0];
+                            for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i]);
+                            kth = mx;
+                        }
                         if (lo <= U) {
-                            const float up = dt + e;
-                            if (kl && up < kth) {
-                                // replace the largest of the row's k best
-                                int m = 0;
-                                for (int i = 1; i < kl; ++i) if (kb[i] > kb[m]) m = i;
-                                kb[m] = up;
-                                float mx = kb[0];
-                                for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i]);
-                                kth = mx;
-                                U = fminf(U, kth);
-                            }
-                            if (lo <= U) {
-                                const int slot = atomicAdd(&A.cand_cnt[q], 1);
-                                if (slot < A.cand_C) {
-                                    A.cand_p[(int64_t)q * A.cand_C + slot] = (int32_t)pos;
-                                    A.cand_lb[(int64_t)q * A.cand_C + slot] = lo;
-                                    ++my_cand;
-                                } else {
-                                    atomicOr(&A.qflag[q], 1);
-                                }
+                            const int slot = atomicAdd(&A.cand_cnt[q], 1);
+                            if (slot < A.cand_C) {
+                                A.cand_p[(int64_t)q * A.cand_C + slot] = (int32_t)(row0 + cb + j);
+                                A.cand_lb[(int64_t)q * A.cand_C + slot] = lo;
+                                ++my_cand;
+                            } else {
+                                atomicOr(&A.qflag[q], 1);
                             }
                         }
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(&S.acc_empty[b]);
-                if (q >= 0 && kth < INFINITY) atomicMin(&A.U[q], __float_as_uint(kth));
+                if (q >= 0 && kth < U) {
+                    U = kth;
+                    atomicMin(&A.U[q], __float_as_uint(kth));
+                }
             }
+            my_pairs += pairs;
         }
         g_tile += T;
         __syncthreads();
@@ -394,11 +439,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     }
 }
 
-// BF16 copy of the leaf-ordered collection in core-matrix order, and the
-// squared norms (binary64 sums of the float32 rows, rounded up) and norms.
+// BF16 copy of the leaf-ordered collection in core-matrix order, and per
+// series {|x|^2 (1 - eb) rounded down, |x| rounded up} from binary64 sums.
 __global__ void k_make_bf16(const float *__restrict__ X, int64_t N, int n, int64_t Npad,
-                            __nv_bfloat16 *__restrict__ Xb, float *__restrict__ x2,
-                            float *__restrict__ xn) {
+                            __nv_bfloat16 *__restrict__ Xb, float2 *__restrict__ xq) {
     const int nk = n / 8;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Npad * nk;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -423,14 +467,14 @@ __global__ void k_make_bf16(const float *__restrict__ X, int64_t N, int n, int64
         double s = 0.0;
         if (i < N)
             for (int j = 0; j < n; ++j) s += (double)X[i * n + j] * (double)X[i * n + j];
-        x2[i] = __double2float_ru(s);
-        xn[i] = __double2float_ru(sqrt(s));
+        xq[i] = make_float2(__double2float_rd(s * (1.0 - kTcEb)), __double2float_ru(sqrt(s)));
     }
 }
 
-// Queries: bfloat16 rows, squared norms and the per-query error coefficient.
-__global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, float c_rel,
-                           __nv_bfloat16 *__restrict__ Qb, float *__restrict__ q2,
+// Queries: bfloat16 rows, |q|^2 (1 - eb) rounded down and the per-query
+// error coefficient c |q| rounded up.
+__global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, double c_rel,
+                           __nv_bfloat16 *__restrict__ Qb, float *__restrict__ q2e,
                            float *__restrict__ qa) {
     const int q = blockIdx.x;
     if (q >= nq) return;
@@ -447,7 +491,7 @@ __global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, float c_r
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        q2[q] = __double2float_ru(t);
+        q2e[q] = __double2float_rd(t * (1.0 - kTcEb));
         qa[q] = __double2float_ru(c_rel * sqrt(t));
     }
 }
@@ -492,8 +536,8 @@ __global__ void k_tc_rescore(const float *__restrict__ Q, const float *__restric
 }
 
 size_t tc_smem_bytes(int n) {
-    return (size_t)kTcM * n * 2 + (size_t)kTcStages * kTcN * n * 2 + (size_t)kTcM * kLocalK * 4 +
-           sizeof(TcShared) + 1024;
+    return (size_t)kTcM * n * 2 + (size_t)kTcStages * kTcN * n * 2 + (size_t)kNormSlots * kTcN * 8 +
+           (size_t)kTcM * kLocalK * 4 + sizeof(TcShared) + 1024;
 }
 
 uint32_t tc_idesc() {
@@ -505,6 +549,8 @@ uint32_t tc_idesc() {
     d |= (uint32_t)(kTcM >> 4) << 24;      // M
     return d;                              // both operands K-major, dense
 }
+
+float tc_eb2() { return (float)(2.0 * kTcEb / (1.0 - kTcEb) * (1.0 + 0x1p-10)); }
 
 double tc_error_coefficient(int n) {
     const double u = std::ldexp(1.0, -8);
@@ -529,18 +575,19 @@ void launch_tc_scan(const TcArgs &a, cudaStream_t s) {
     HK_CHECK_LAUNCH();
 }
 
-void launch_make_bf16(const float *X, int64_t N, int n, int64_t Npad, void *Xb, float *x2, float *xn,
+void launch_make_bf16(const float *X, int64_t N, int n, int64_t Npad, void *Xb, void *xq,
                       cudaStream_t s) {
     int dev = 0, sms = 0;
     HK_CHECK_CUDA(cudaGetDevice(&dev));
     HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    k_make_bf16<<<sms * 16, 256, 0, s>>>(X, N, n, Npad, reinterpret_cast<__nv_bfloat16 *>(Xb), x2, xn);
+    k_make_bf16<<<sms * 16, 256, 0, s>>>(X, N, n, Npad, reinterpret_cast<__nv_bfloat16 *>(Xb),
+                                         reinterpret_cast<float2 *>(xq));
     HK_CHECK_LAUNCH();
 }
 
-void launch_tc_qprep(const float *Q, int nq, int n, double c_rel, void *Qb, float *q2, float *qa,
+void launch_tc_qprep(const float *Q, int nq, int n, double c_rel, void *Qb, float *q2e, float *qa,
                      cudaStream_t s) {
-    k_tc_qprep<<<nq, 128, 0, s>>>(Q, nq, n, (float)c_rel, reinterpret_cast<__nv_bfloat16 *>(Qb), q2, qa);
+    k_tc_qprep<<<nq, 128, 0, s>>>(Q, nq, n, c_rel, reinterpret_cast<__nv_bfloat16 *>(Qb), q2e, qa);
     HK_CHECK_LAUNCH();
 }
 
