@@ -184,8 +184,8 @@ def main():
     ap.add_argument("--query-group", type=int, default=0)
     ap.add_argument("--series-tile", type=int, default=0)
     ap.add_argument("--l-max", type=int, default=0)
-    ap.add_argument("--form", default="plain", choices=["plain", "bf16"],
-                    help="plain float32 scan, or the bfloat16 tensor-core form")
+    ap.add_argument("--form", default="plain", choices=["plain", "bf16", "fp16"],
+                    help="plain float32 scan, or the tensor-core form on a bfloat16 / float16 copy")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
@@ -219,8 +219,8 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sample = X[:min(N, 4_000_000)].cpu().numpy()
     t0 = time.perf_counter()
-    bflags = binding.HK_BUILD_BF16 if args.form == "bf16" else 0
-    qflags = binding.HK_Q_TIMING | (binding.HK_Q_BF16 if args.form == "bf16" else 0)
+    bflags = {"plain": 0, "bf16": binding.HK_BUILD_BF16, "fp16": binding.HK_BUILD_FP16}[args.form]
+    qflags = binding.HK_Q_TIMING | (binding.HK_Q_BF16 if args.form != "plain" else 0)
     idx = binding.Index(X, wl["tau"], flags=bflags)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0

@@ -50,7 +50,10 @@ typedef struct hk_index hk_index;
                               index takes over and frees once it no longer
                               needs it (saves one copy of the collection).  */
 #define HK_BUILD_BF16 2u   /* also keep a bfloat16 copy of the collection
-                              and binary64 squared norms (precision form).  */
+                              and its norms (precision form).               */
+#define HK_BUILD_FP16 4u   /* the same with float16 instead (three more bits
+                              of precision; values must fit float16:
+                              |x| <= 65504, else HK_EINVAL)                 */
 
 typedef struct {
     int32_t leaf_capacity;  /* tau, the leaf threshold (Sec. 3.2); >= 1      */
@@ -98,9 +101,9 @@ int hk_index_info_get(const hk_index *idx, hk_index_info *out);
 #define HK_Q_TIMING 8u     /* time the scan kernels with CUDA events on the
                               call's stream (hk_query_stats.scan_ns)          */
 #define HK_Q_BF16 16u      /* precision form: distances of the candidate
-                              leaves on the tensor cores from the bfloat16
-                              copy (index built with HK_BUILD_BF16, n <= 256),
-                              certified error bound, exact rescore           */
+                              leaves on the tensor cores from the index's
+                              16-bit copy (HK_BUILD_BF16 or HK_BUILD_FP16,
+                              n <= 256), certified error bound, exact rescore */
 
 typedef struct {
     int32_t l_max;        /* leaves visited by the approximate search per query

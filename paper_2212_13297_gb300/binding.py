@@ -25,6 +25,7 @@ HK_EINTERNAL = -6
 
 HK_BUILD_ADOPT = 1
 HK_BUILD_BF16 = 2
+HK_BUILD_FP16 = 4
 HK_Q_NOSAX = 1
 HK_Q_NOTHRESH = 2
 HK_Q_NOPRUNE = 4

@@ -74,6 +74,8 @@ int hk_build(const float *X, int64_t N, int32_t n, const hk_build_opts *opts, vo
         }
         if (o.leaf_capacity < 1) hk::fail(HK_EINVAL, "leaf_capacity=%d must be >= 1", o.leaf_capacity);
         if (o.eval_cap < 0) hk::fail(HK_EINVAL, "eval_cap=%d must be >= 0", o.eval_cap);
+        if ((o.flags & HK_BUILD_BF16) && (o.flags & HK_BUILD_FP16))
+            hk::fail(HK_EINVAL, "HK_BUILD_BF16 and HK_BUILD_FP16 exclude each other");
         cudaStream_t s = (cudaStream_t)stream;
         const bool dev = hk::is_device_ptr(X);
         if ((o.flags & HK_BUILD_ADOPT) && !dev) hk::fail(HK_EINVAL, "HK_BUILD_ADOPT needs a device X");
@@ -135,7 +137,8 @@ int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k, const hk_quer
         if (o.l_max < 0) hk::fail(HK_EINVAL, "l_max=%d must be >= 0", o.l_max);
         if (o.query_group < 0 || o.series_tile < 0) hk::fail(HK_EINVAL, "tile sizes must be >= 0");
         if (o.flags & HK_Q_BF16) {
-            if (!idx->has_bf16) hk::fail(HK_EINVAL, "HK_Q_BF16 needs an index built with HK_BUILD_BF16");
+            if (!idx->has_bf16)
+                hk::fail(HK_EINVAL, "HK_Q_BF16 needs an index built with HK_BUILD_BF16 or HK_BUILD_FP16");
             if (idx->n > hk::kTcMaxLen)
                 hk::fail(HK_EINVAL, "HK_Q_BF16 takes series of length <= %d (n=%d)", hk::kTcMaxLen, idx->n);
             if (o.flags & HK_Q_NOPRUNE) hk::fail(HK_EINVAL, "HK_Q_BF16 and HK_Q_NOPRUNE exclude each other");
@@ -206,7 +209,7 @@ int hk_debug_lb_sax(hk_index *idx, const float *Q, int32_t nq, float *out) {
 int hk_debug_tc_dist(hk_index *idx, const float *Q, int32_t nq, float *lo, float *up) {
     return guard([&] {
         if (!idx || !Q || !lo || !up || nq < 1) hk::fail(HK_EINVAL, "bad argument");
-        if (!idx->has_bf16) hk::fail(HK_EINVAL, "index built without HK_BUILD_BF16");
+        if (!idx->has_bf16) hk::fail(HK_EINVAL, "index built without a 16-bit copy");
         if (idx->n > hk::kTcMaxLen) hk::fail(HK_EINVAL, "n=%d > %d", idx->n, hk::kTcMaxLen);
         hk::DevBuf<float> tmp;
         const float *Qd = device_view(Q, (size_t)nq * idx->n, idx->stream, tmp);

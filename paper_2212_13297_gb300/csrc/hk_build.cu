@@ -22,6 +22,7 @@
 // candidate stays a leaf.  All of it in binary64 with the operation order
 // written here.
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <utility>
 
@@ -658,13 +659,27 @@ void build_index(hk_index *idx, const float *Xsrc, int64_t N, int n, const hk_bu
     idx->sax.alloc((size_t)N * kWord, s);
     k_isax<<<grid_for(N, 256, sms), 256, 0, s>>>(idx->X.p, n, N, idx->bp.p, idx->sax.p);
     HK_CHECK_LAUNCH();
-    if (o.flags & HK_BUILD_BF16) {
-        // bfloat16 copy for the tensor-core form: rows padded so a 128-series
+    if (o.flags & (HK_BUILD_BF16 | HK_BUILD_FP16)) {
+        // 16-bit copy for the tensor-core form: rows padded so a 128-series
         // tile starting at any 8-aligned position stays inside the buffer
+        const int fmt = (o.flags & HK_BUILD_FP16) ? kFmtF16 : kFmtBF16;
         idx->Npad = ((N + 7) / 8) * 8 + 136;
         idx->Xb.alloc((size_t)idx->Npad * n, s);
         idx->xq.alloc(idx->Npad, s);
-        launch_make_bf16(idx->X.p, N, n, idx->Npad, idx->Xb.p, idx->xq.p, s);
+        DevBuf<unsigned> flags;
+        flags.alloc(2, s);
+        HK_CHECK_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(unsigned), s));
+        launch_make_16(idx->X.p, N, n, idx->Npad, fmt, idx->Xb.p, idx->xq.p,
+                       reinterpret_cast<int *>(flags.p), s);
+        launch_max_norm(idx->xq.p, N, flags.p + 1, s);
+        unsigned h[2];
+        HK_CHECK_CUDA(cudaMemcpyAsync(h, flags.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (h[0]) fail(HK_EINVAL, "HK_BUILD_FP16: the collection has values beyond float16's range");
+        float xm;
+        std::memcpy(&xm, &h[1], 4);
+        idx->xn_max = (double)xm;
+        idx->fmt16 = fmt;
         idx->has_bf16 = true;
     }
     HK_CHECK_CUDA(cudaStreamSynchronize(s));

@@ -119,7 +119,8 @@ struct Workspace {
     DevBuf<float> out_dist;     // nq * k
     DevBuf<int32_t> approx;     // nq * A
     DevBuf<uint16_t> Qb;        // bfloat16 queries (tensor-core form)
-    DevBuf<float> q2, qa;       // query |q|^2 (1-eb) rounded down, error coefficients
+    DevBuf<float> q2, qa, qoff; // query |q|^2 (1-eb) - abs term, error coefficient, 2 x abs term
+    DevBuf<int> bad;            // a query outside the 16-bit format's range
     DevBuf<int32_t> cand_cnt;   // nq    tensor-core candidates per query
     DevBuf<int32_t> cand_p;     // nq * cand_C
     DevBuf<float> cand_lb;      // nq * cand_C  lower bound D~ - E
@@ -165,7 +166,9 @@ struct hk_index {
     hk::DevBuf<uint16_t> Xb;       // bfloat16 copy in core-matrix order (HK_BUILD_BF16)
     hk::DevBuf<float2> xq;         // {|x|^2 (1-eb) rounded down, |x| rounded up} per series
     int64_t Npad = 0;
-    bool has_bf16 = false;
+    bool has_bf16 = false;         // a 16-bit copy exists (format fmt16)
+    int fmt16 = 1;                 // kFmtBF16 or kFmtF16
+    double xn_max = 0.0;           // largest |x| (rounded up)
 
     std::vector<int64_t> h_leaf_off;
     std::vector<int32_t> h_leaf_nseg;
@@ -222,7 +225,8 @@ struct TcArgs {
     const float2 *xq;            // per position: {|x|^2 (1-eb) rounded down, |x| rounded up}
     int n;
     const uint16_t *Qb;          // bfloat16 queries, row-major
-    const float *q2e, *qa;       // per query: |q|^2 (1-eb) rounded down, c |q| rounded up
+    const float *q2e, *qa;       // per query: |q|^2 (1-eb) - abs term rounded down, c |q| rounded up
+    const float *qoff2;          // per query: twice the absolute error term
     float eb2;                   // 2 eb / (1 - eb) with margin: the upper bound's norm term
     const int64_t *leaf_off;
     int64_t L;
@@ -244,17 +248,20 @@ struct TcArgs {
     int64_t N;
 };
 void launch_tc_scan(const TcArgs &a, cudaStream_t s);
-void launch_make_bf16(const float *X, int64_t N, int n, int64_t Npad, void *Xb, void *xq,
-                      cudaStream_t s);
-void launch_tc_qprep(const float *Q, int nq, int n, double c_rel, void *Qb, float *q2e, float *qa,
-                     cudaStream_t s);
+constexpr int kFmtF16 = 0;    // tcgen05 kind::f16 operand encodings
+constexpr int kFmtBF16 = 1;
+void launch_make_16(const float *X, int64_t N, int n, int64_t Npad, int fmt, void *Xb, void *xq,
+                    int *bad, cudaStream_t s);
+void launch_tc_qprep(const float *Q, int nq, int n, int fmt, double xn_max, void *Qb, float *q2e,
+                     float *qa, float *qoff2, int *bad, cudaStream_t s);
 void launch_tc_rescore(const float *Q, const float *X, int n, int nq, const int32_t *cand_cnt,
                        const int32_t *cand_p, const float *cand_lb, int cand_C, const uint32_t *U,
                        float *pool_d, int32_t *pool_p, int32_t *pool_cnt, int pool_C, int32_t *qflag,
                        long long *stats, int stat_slot, cudaStream_t s);
 size_t tc_smem_bytes(int n);
-uint32_t tc_idesc();
-double tc_error_coefficient(int n);
+void launch_max_norm(const void *xq, int64_t N, unsigned *out, cudaStream_t s);
+uint32_t tc_idesc(int fmt);
+double tc_error_coefficient(int n, int fmt);
 float tc_eb2();
 constexpr int kTcMaxLen = 256;     // longest series the tensor-core form takes
 

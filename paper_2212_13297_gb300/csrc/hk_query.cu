@@ -1067,7 +1067,15 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         ws.Qb.reserve((size_t)nq * n, s);
         ws.q2.reserve(nq, s);
         ws.qa.reserve(nq, s);
-        launch_tc_qprep(Qd, nq, n, tc_error_coefficient(n), ws.Qb.p, ws.q2.p, ws.qa.p, s);
+        ws.qoff.reserve(nq, s);
+        ws.bad.reserve(1, s);
+        HK_CHECK_CUDA(cudaMemsetAsync(ws.bad.p, 0, sizeof(int), s));
+        launch_tc_qprep(Qd, nq, n, idx->fmt16, idx->xn_max, ws.Qb.p, ws.q2.p, ws.qa.p, ws.qoff.p,
+                        ws.bad.p, s);
+        int bad = 0;
+        HK_CHECK_CUDA(cudaMemcpyAsync(&bad, ws.bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (bad) fail(HK_EINVAL, "queries have values beyond the 16-bit copy's range");
     }
     // a1 + a2
     k_qprep<<<nq, 256, n * sizeof(float), s>>>(Qd, n, idx->seg_ab.p, idx->S, idx->bp.p, ws.qseg.p,
@@ -1155,6 +1163,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         t.Qb = ws.Qb.p;
         t.q2e = ws.q2.p;
         t.qa = ws.qa.p;
+        t.qoff2 = ws.qoff.p;
         t.eb2 = tc_eb2();
         t.leaf_off = v.leaf_off;
         t.L = L;
@@ -1174,7 +1183,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         t.stats = (long long *)ws.stats.p;
         t.stat_pairs = ST_TC_PAIRS;
         t.stat_cands = ST_TC_CANDS;
-        t.idesc = tc_idesc();
+        t.idesc = tc_idesc(idx->fmt16);
         t.dbg_lo = nullptr;
         t.dbg_up = nullptr;
         t.N = idx->N;
@@ -1426,7 +1435,10 @@ void debug_tc_dist(hk_index *idx, const float *Qd, int nq, float *lo_host, float
     ws.Qb.reserve((size_t)nq * n, s);
     ws.q2.reserve(nq, s);
     ws.qa.reserve(nq, s);
-    launch_tc_qprep(Qd, nq, n, tc_error_coefficient(n), ws.Qb.p, ws.q2.p, ws.qa.p, s);
+    ws.qoff.reserve(nq, s);
+    ws.bad.reserve(1, s);
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.bad.p, 0, sizeof(int), s));
+    launch_tc_qprep(Qd, nq, n, idx->fmt16, idx->xn_max, ws.Qb.p, ws.q2.p, ws.qa.p, ws.qoff.p, ws.bad.p, s);
     reserve_common(ws, nq, L, 1, 1, s);
     HK_CHECK_CUDA(cudaMemsetAsync(ws.mask.p, 2, (size_t)L * nq, s));
     k_fill_u32<<<64, 256, 0, s>>>(ws.U.p, nq, 0x7f800000u);
@@ -1455,6 +1467,7 @@ void debug_tc_dist(hk_index *idx, const float *Qd, int nq, float *lo_host, float
     t.Qb = ws.Qb.p;
     t.q2e = ws.q2.p;
     t.qa = ws.qa.p;
+    t.qoff2 = ws.qoff.p;
     t.eb2 = tc_eb2();
     t.leaf_off = v.leaf_off;
     t.L = L;
@@ -1472,7 +1485,7 @@ void debug_tc_dist(hk_index *idx, const float *Qd, int nq, float *lo_host, float
     t.qflag = ws.qflag.p;
     t.err = ws.counters.p + 2;
     t.stats = nullptr;
-    t.idesc = tc_idesc();
+    t.idesc = tc_idesc(idx->fmt16);
     t.dbg_lo = dlo.p;
     t.dbg_up = dup.p;
     t.N = N;

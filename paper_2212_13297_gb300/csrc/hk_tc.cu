@@ -1,10 +1,14 @@
 // Precision form: squared distances on the tcgen05 tensor cores.
 //
+// The 16-bit copy is bfloat16 (the default) or float16 (HK_BUILD_FP16: three
+// more bits of precision for collections inside float16's range).
+//
 // For a block of up to 128 queries and a run of series, D~(q,x) =
 // |q|^2 + |x|^2 - 2 q^.x^ with q^, x^ the bfloat16 roundings and the dot
 // products accumulated in float32 in tensor memory.  Each D~ carries a
 // certified error bound E(q,x) = A_q |x| + B (|q|^2 + |x|^2):
-//   |q^.x^ - q.x| <= (2u + u^2 + g(1+u)^2) |q||x|,  u = 2^-8 (bfloat16),
+//   |q^.x^ - q.x| <= (2u + u^2 + g(1+u)^2) |q||x| + (subnormal term),
+//   u = 2^-8 (bfloat16) or 2^-11 (float16),
 //   g = n w / (1 - n w), w = 2^-20 (a pessimistic per-addition error of the
 //   float32 accumulation, allowing truncating adders),
 // doubled for the -2 factor, plus a relative term covering the float32
@@ -54,7 +58,8 @@ constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTmemCols = 256;   // two accumulators of kTcN columns
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far above any legitimate wait
 constexpr int kLocalK = 32;
-constexpr double kTcEb = 0x1p-19;   // relative term for norm and epilogue rounding      // 2k up to this tightens U per row
+constexpr double kTcEb = 0x1p-19;   // relative term for norm and epilogue rounding
+constexpr float kF16Max = 65504.0f;      // 2k up to this tightens U per row
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -315,10 +320,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
             const int r = (warp & 3) * 32 + lane;   // TMEM lane quarter of this warp
             const int half = (warp - 2) >> 2;       // column half
             const int q = S.qid[r];
-            float q2e = 0.f, qa = 0.f, U = 0.f;
+            float q2e = 0.f, qa = 0.f, qoff2 = 0.f, U = 0.f;
             if (q >= 0) {
                 q2e = A.q2e[q];
                 qa = A.qa[q];
+                qoff2 = A.qoff2[q];
                 U = __uint_as_float(A.U[q]);
             }
             float *kb = kbest + r * kLocalK;
@@ -369,7 +375,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                             const float bs = lo + 2.0f * qa * xv.y;
                             A.dbg_lo[(int64_t)q * A.N + row0 + cb + j] = lo;
                             A.dbg_up[(int64_t)q * A.N + row0 + cb + j] =
-                                bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x);
+                                bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
                         }
                     }
                     while (hit) {
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                         const float2 xv = xs[cb + j];
                         const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
                         const float bs = lo + 2.0f * qa * xv.y;
-                        const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x);
+                        const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
                         if (kl && up < kth) {
                             int m = 0;
                             for (int i = 1; i < kl; ++i) if (kb[i] > kb[m]) m = i;
@@ -439,25 +445,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     }
 }
 
-// BF16 copy of the leaf-ordered collection in core-matrix order, and per
-// series {|x|^2 (1 - eb) rounded down, |x| rounded up} from binary64 sums.
-__global__ void k_make_bf16(const float *__restrict__ X, int64_t N, int n, int64_t Npad,
-                            __nv_bfloat16 *__restrict__ Xb, float2 *__restrict__ xq) {
+// 16-bit copy (bfloat16 or float16) of the leaf-ordered collection in
+// core-matrix order, and per series {|x|^2 (1 - eb) rounded down, |x|
+// rounded up} from binary64 sums.  Values a float16 cannot hold set *bad.
+__device__ __forceinline__ uint16_t to16(float v, int fmt) {
+    if (fmt == kFmtBF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    return __half_as_ushort(__float2half_rn(v));
+}
+
+__global__ void k_make_16(const float *__restrict__ X, int64_t N, int n, int64_t Npad, int fmt,
+                          uint16_t *__restrict__ Xb, float2 *__restrict__ xq, int *__restrict__ bad) {
     const int nk = n / 8;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Npad * nk;
          c += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = c / nk;
         const int k8 = (int)(c % nk);
-        __nv_bfloat16 h[8];
+        uint16_t h[8];
         if (i < N) {
             const float4 a = *reinterpret_cast<const float4 *>(X + i * n + k8 * 8);
             const float4 b = *reinterpret_cast<const float4 *>(X + i * n + k8 * 8 + 4);
-            h[0] = __float2bfloat16_rn(a.x); h[1] = __float2bfloat16_rn(a.y);
-            h[2] = __float2bfloat16_rn(a.z); h[3] = __float2bfloat16_rn(a.w);
-            h[4] = __float2bfloat16_rn(b.x); h[5] = __float2bfloat16_rn(b.y);
-            h[6] = __float2bfloat16_rn(b.z); h[7] = __float2bfloat16_rn(b.w);
+            const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                if (fmt == kFmtF16 && fabsf(f[e]) > kF16Max) *bad = 1;
+                h[e] = to16(f[e], fmt);
+            }
         } else {
-            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(0.0f);
+            for (int e = 0; e < 8; ++e) h[e] = 0;
         }
         const int64_t off = (((i >> 3) * nk + k8) * 8 + (i & 7)) * 8;
         *reinterpret_cast<uint4 *>(Xb + off) = *reinterpret_cast<const uint4 *>(h);
@@ -471,18 +485,21 @@ __global__ void k_make_bf16(const float *__restrict__ X, int64_t N, int n, int64
     }
 }
 
-// Queries: bfloat16 rows, |q|^2 (1 - eb) rounded down and the per-query
-// error coefficient c |q| rounded up.
-__global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, double c_rel,
-                           __nv_bfloat16 *__restrict__ Qb, float *__restrict__ q2e,
-                           float *__restrict__ qa) {
+// Queries: 16-bit rows, |q|^2 (1 - eb) lowered by the query's absolute
+// error term (rounded down), the coefficient c |q| (rounded up) and twice
+// the absolute term (for the interval's upper end).
+__global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, int fmt, double c_rel,
+                           double abs_unit, double xn_max, uint16_t *__restrict__ Qb,
+                           float *__restrict__ q2e, float *__restrict__ qa, float *__restrict__ qoff2,
+                           int *__restrict__ bad) {
     const int q = blockIdx.x;
     if (q >= nq) return;
     __shared__ double red[32];
     double s = 0.0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const float v = Q[(int64_t)q * n + j];
-        Qb[(int64_t)q * n + j] = __float2bfloat16_rn(v);
+        if (fmt == kFmtF16 && fabsf(v) > kF16Max) *bad = 1;
+        Qb[(int64_t)q * n + j] = to16(v, fmt);
         s += (double)v * (double)v;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -491,8 +508,15 @@ __global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, double c_
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        q2e[q] = __double2float_rd(t * (1.0 - kTcEb));
-        qa[q] = __double2float_ru(c_rel * sqrt(t));
+        const double qn = sqrt(t);
+        // sum_j |q^_j x^_j - q_j x_j| beyond the relative term: at most
+        // a (|q_j| (2+u) + |x_j| (1+u)) + a^2 per point, a the half spacing
+        // of the format's subnormals; summed and doubled for the -2 factor
+        const double off = 2.0 * (abs_unit * sqrt((double)n) * (2.01 * qn + 1.01 * xn_max) +
+                                  (double)n * abs_unit * abs_unit);
+        q2e[q] = __double2float_rd(t * (1.0 - kTcEb) - off);
+        qa[q] = __double2float_ru(c_rel * qn);
+        qoff2[q] = __double2float_ru(2.0 * off);
     }
 }
 
@@ -540,11 +564,11 @@ size_t tc_smem_bytes(int n) {
            (size_t)kTcM * kLocalK * 4 + sizeof(TcShared) + 1024;
 }
 
-uint32_t tc_idesc() {
+uint32_t tc_idesc(int fmt) {
     uint32_t d = 0;
     d |= 1u << 4;                          // D format: float32
-    d |= 1u << 7;                          // A format: bfloat16
-    d |= 1u << 10;                         // B format: bfloat16
+    d |= (uint32_t)fmt << 7;               // A format: 0 float16, 1 bfloat16
+    d |= (uint32_t)fmt << 10;              // B format: the same as A
     d |= (uint32_t)(kTcN >> 3) << 17;      // N
     d |= (uint32_t)(kTcM >> 4) << 24;      // M
     return d;                              // both operands K-major, dense
@@ -552,8 +576,8 @@ uint32_t tc_idesc() {
 
 float tc_eb2() { return (float)(2.0 * kTcEb / (1.0 - kTcEb) * (1.0 + 0x1p-10)); }
 
-double tc_error_coefficient(int n) {
-    const double u = std::ldexp(1.0, -8);
+double tc_error_coefficient(int n, int fmt) {
+    const double u = std::ldexp(1.0, fmt == kFmtBF16 ? -8 : -11);   // unit roundoff of the format
     const double w = std::ldexp(1.0, -20);
     const double g = n * w / (1.0 - n * w);
     const double c1 = 2 * u + u * u + g * (1 + u) * (1 + u);
@@ -575,19 +599,39 @@ void launch_tc_scan(const TcArgs &a, cudaStream_t s) {
     HK_CHECK_LAUNCH();
 }
 
-void launch_make_bf16(const float *X, int64_t N, int n, int64_t Npad, void *Xb, void *xq,
-                      cudaStream_t s) {
+double tc_abs_unit(int fmt) {
+    // half the spacing of the format's subnormals
+    return std::ldexp(1.0, fmt == kFmtBF16 ? -134 : -25);
+}
+
+void launch_make_16(const float *X, int64_t N, int n, int64_t Npad, int fmt, void *Xb, void *xq,
+                    int *bad, cudaStream_t s) {
     int dev = 0, sms = 0;
     HK_CHECK_CUDA(cudaGetDevice(&dev));
     HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    k_make_bf16<<<sms * 16, 256, 0, s>>>(X, N, n, Npad, reinterpret_cast<__nv_bfloat16 *>(Xb),
-                                         reinterpret_cast<float2 *>(xq));
+    k_make_16<<<sms * 16, 256, 0, s>>>(X, N, n, Npad, fmt, reinterpret_cast<uint16_t *>(Xb),
+                                       reinterpret_cast<float2 *>(xq), bad);
     HK_CHECK_LAUNCH();
 }
 
-void launch_tc_qprep(const float *Q, int nq, int n, double c_rel, void *Qb, float *q2e, float *qa,
-                     cudaStream_t s) {
-    k_tc_qprep<<<nq, 128, 0, s>>>(Q, nq, n, c_rel, reinterpret_cast<__nv_bfloat16 *>(Qb), q2e, qa);
+void launch_tc_qprep(const float *Q, int nq, int n, int fmt, double xn_max, void *Qb, float *q2e,
+                     float *qa, float *qoff2, int *bad, cudaStream_t s) {
+    k_tc_qprep<<<nq, 128, 0, s>>>(Q, nq, n, fmt, tc_error_coefficient(n, fmt), tc_abs_unit(fmt), xn_max,
+                                  reinterpret_cast<uint16_t *>(Qb), q2e, qa, qoff2, bad);
+    HK_CHECK_LAUNCH();
+}
+
+__global__ void k_max_norm(const float2 *__restrict__ xq, int64_t N, unsigned *__restrict__ out) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, xq[i].y);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+void launch_max_norm(const void *xq, int64_t N, unsigned *out, cudaStream_t s) {
+    k_max_norm<<<256, 256, 0, s>>>(reinterpret_cast<const float2 *>(xq), N, out);
     HK_CHECK_LAUNCH();
 }
 

@@ -30,14 +30,15 @@ def _wl():
     return workload
 
 
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
 @pytest.mark.parametrize("N,n,kind", [(3000, 256, "rw"), (2500, 64, "rw"), (2000, 96, "gauss"),
                                       (1800, 128, "rw")])
-def test_tc_distance_within_certified_bound(hb, N, n, kind):
+def test_tc_distance_within_certified_bound(hb, N, n, kind, fmt):
     wl = _wl()
     X = wl.random_walk(N, n, seed=N, device="cuda") if kind == "rw" else \
         wl.gaussian(N, n, seed=N, device="cuda")
     Q, _ = wl.queries(X, 9, [0.01, 0.5, 1.0], seed=3, norm="z" if kind == "rw" else None)
-    idx = hb.Index(X, 100, flags=hb.HK_BUILD_BF16)
+    idx = hb.Index(X, 100, flags=hb.HK_BUILD_BF16 if fmt == "bf16" else hb.HK_BUILD_FP16)
     assert idx.info()["has_bf16"] == 1
     ex = idx.export()
     lo, up = idx.debug_tc_dist(Q)
@@ -51,21 +52,23 @@ def test_tc_distance_within_certified_bound(hb, N, n, kind):
     # distances, and the bfloat16 rounding uses a visible part of it
     half = (up.astype(np.float64) - lo) / 2
     mid = (up.astype(np.float64) + lo) / 2
-    assert float(np.median(half / exact)) < 0.05
-    assert 0.01 < float(np.median(np.abs(mid - exact) / half)) < 0.5
+    assert float(np.median(half / exact)) < (0.05 if fmt == "bf16" else 0.008)
+    assert (0.01 if fmt == "bf16" else 0.002) < float(np.median(np.abs(mid - exact) / half)) < 0.5
 
 
-@pytest.mark.parametrize("N,n,tau,nq,k,sig", [
-    (20000, 256, 300, 20, 10, [0.5, 1.0]),
-    (20000, 256, 300, 150, 1, [0.3, 1.0]),
-    (15000, 64, 200, 30, 50, [0.1, 1.0]),
-    (12000, 96, 150, 16, 5, [0.5]),
+@pytest.mark.parametrize("N,n,tau,nq,k,sig,fmt", [
+    (20000, 256, 300, 20, 10, [0.5, 1.0], "bf16"),
+    (20000, 256, 300, 150, 1, [0.3, 1.0], "bf16"),
+    (15000, 64, 200, 30, 50, [0.1, 1.0], "bf16"),
+    (12000, 96, 150, 16, 5, [0.5], "bf16"),
+    (20000, 256, 300, 150, 10, [0.01, 0.5, 1.0], "fp16"),
+    (15000, 128, 200, 30, 50, [0.1, 1.0], "fp16"),
 ])
-def test_tc_query_matches_bruteforce(hb, oracle_lib, N, n, tau, nq, k, sig):
+def test_tc_query_matches_bruteforce(hb, oracle_lib, N, n, tau, nq, k, sig, fmt):
     wl = _wl()
     X = wl.random_walk(N, n, seed=N + n, device="cuda")
     Q, _ = wl.queries(X, nq, sig, seed=k)
-    idx = hb.Index(X, tau, flags=hb.HK_BUILD_BF16)
+    idx = hb.Index(X, tau, flags=hb.HK_BUILD_BF16 if fmt == "bf16" else hb.HK_BUILD_FP16)
     ids, dist, st = idx.query(Q, k, flags=hb.HK_Q_BF16)
     oids, od2 = oracle.knn(X.cpu().numpy(), Q.cpu().numpy(), k)
     np.testing.assert_array_equal(ids.cpu().numpy(), oids)
@@ -91,15 +94,31 @@ def test_tc_ties_and_flag_checks(hb, oracle_lib):
     assert e.value.code == hb.HK_EINVAL
 
 
-def test_tc_long_items_match_bruteforce(hb, oracle_lib):
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_tc_long_items_match_bruteforce(hb, oracle_lib, fmt):
     """Items spanning many tiles (so the producer, MMA and epilogue run
     several tiles apart) on hard queries with bounds tightening in flight."""
     wl = _wl()
     X = wl.random_walk(400_000, 256, seed=77, device="cuda")
     Q, _ = wl.queries(X, 160, [0.5, 1.0], seed=78)
-    idx = hb.Index(X, 20_000, flags=hb.HK_BUILD_BF16)
+    idx = hb.Index(X, 20_000, flags=hb.HK_BUILD_BF16 if fmt == "bf16" else hb.HK_BUILD_FP16)
     ids, dist, st = idx.query(Q, 10, flags=hb.HK_Q_BF16)
     sel = np.arange(0, 160, 8)
     oids, od2 = oracle.knn(X.cpu().numpy(), Q.cpu().numpy()[sel], 10)
     np.testing.assert_array_equal(ids.cpu().numpy()[sel], oids)
     np.testing.assert_allclose(dist.cpu().numpy()[sel], np.sqrt(od2).astype(np.float32), rtol=1e-5)
+
+
+def test_fp16_range_checked(hb):
+    wl = _wl()
+    X = wl.random_walk(2000, 64, seed=5, device="cuda")
+    Xb = X.clone()
+    Xb[7, 3] = 70000.0
+    with pytest.raises(hb.HerculesError) as e:
+        hb.Index(Xb, 100, flags=hb.HK_BUILD_FP16)
+    assert e.value.code == hb.HK_EINVAL
+    idx = hb.Index(X, 100, flags=hb.HK_BUILD_FP16)
+    Q = X[:2].clone()
+    Q[1, 0] = -1e5
+    with pytest.raises(hb.HerculesError):
+        idx.query(Q, 3, flags=hb.HK_Q_BF16)
