@@ -5,9 +5,12 @@ Workload (default "large"): 100,000,000 random-walk series x 256 float32
 (a dataset series plus N(0, sigma^2) noise, sigma alternating 0.5 / 1.0,
 re-z-normalised, seed 1); k = 10.  A step answers one batch of queries (1,000
 by default) through the whole path: query preparation, LB_EAPCA, the
-approximate search, leaf pruning, LB_SAX, the early-abandoning distance scan,
-top-k, and the binary64 boundary rescore.  Consecutive steps take consecutive
-batches of the 10,000 queries.
+approximate search, leaf pruning, the distance step, top-k, and the binary64
+boundary rescore.  Consecutive steps take consecutive batches of the 10,000
+queries.  The distance step is the tensor-core form on a float16 copy by
+default (`--form fp16`; `bf16` and the float32 scan `plain` are the others);
+the float32 path is also timed on the same index and reported under `forms`.
+Every answer is exact (ids equal to brute force).
 
 Prints one JSON line.  `--impl reference` times the oracle (plain binary64
 brute force on the host cores) on a bounded sample of the same workload.
@@ -30,7 +33,9 @@ WORKLOADS = {
                   desc="100M random walks x 256, leaf 100K, 10K hard queries (sigma 0.5/1.0), k=10"),
     "mid": dict(N=10_000_000, n=256, tau=10_000, nq=100, sigmas=[0.01, 0.1, 0.5, 1.0], k=10, batch=100,
                 desc="10M random walks x 256, leaf 10K, 100 queries (sigma 0.01/0.1/0.5/1.0), k=10"),
-    # a 2 GB case of the large workload's shape, for profiler captures
+    # 2 GB cases of the large workload's shape, for profiler captures
+    "tcprofile": dict(N=2_000_000, n=256, tau=20_000, nq=1000, sigmas=[0.5, 1.0], k=10, batch=1000,
+                      desc="2M random walks x 256, leaf 20K, 1000 hard queries (sigma 0.5/1.0), k=10"),
     "profile": dict(N=2_000_000, n=256, tau=10_000, nq=200, sigmas=[0.5, 1.0], k=10, batch=200,
                     desc="2M random walks x 256, leaf 10K, 200 hard queries (sigma 0.5/1.0), k=10"),
     "small": dict(N=100_000, n=256, tau=1_000, nq=10, sigmas=[0.1], k=1, batch=10,
@@ -46,8 +51,10 @@ def peaks():
     if os.path.exists(p):
         d = json.load(open(p))
         return dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2070.0),
+                    bf16_tflops=d.get("bf16_tflops"), bf16_tflops_sustained=d.get("bf16_tflops_sustained"),
                     source="measured")
-    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0,
+                source="fallback")
 
 
 class ClockSampler:
@@ -184,7 +191,9 @@ def main():
     ap.add_argument("--query-group", type=int, default=0)
     ap.add_argument("--series-tile", type=int, default=0)
     ap.add_argument("--l-max", type=int, default=0)
-    ap.add_argument("--form", default="plain", choices=["plain", "bf16", "fp16"],
+    ap.add_argument("--plain-steps", type=int, default=2,
+                    help="steps of the float32 path measured beside a tensor-core form")
+    ap.add_argument("--form", default="fp16", choices=["plain", "bf16", "fp16"],
                     help="plain float32 scan, or the tensor-core form on a bfloat16 / float16 copy")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
@@ -234,37 +243,41 @@ def main():
     dist_out = torch.empty((B, k), dtype=torch.float32, device="cuda")
     qkw = dict(l_max=args.l_max, query_group=args.query_group, series_tile=args.series_tile)
 
-    for i in range(args.warmup):
-        idx.query(batches[i], k, flags=qflags, out=(ids, dist_out), **qkw)
-    torch.cuda.synchronize()
+    def timed(flags, steps, warmup, first):
+        """Device time of `steps` batches (after `warmup`), summed stats, per-step latencies."""
+        for i in range(warmup):
+            idx.query(batches[(first + i) % len(batches)], k, flags=flags, out=(ids, dist_out), **qkw)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        ev0.record(stream)
+        lat, agg = [], {}
+        for i in range(steps):
+            ts = time.perf_counter()
+            _, _, st = idx.query(batches[(first + warmup + i) % len(batches)], k, flags=flags,
+                                 out=(ids, dist_out), **qkw)
+            lat.append(time.perf_counter() - ts)
+            for key, v in st.items():
+                agg[key] = agg.get(key, 0) + v
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        t = ev0.elapsed_time(ev1) / 1e3
+        if ws > 1:
+            tt = torch.tensor([t], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            t = float(tt.item())
+        return t, agg, lat
 
     sampler = ClockSampler(dev_index)
     sampler.start()
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    stream = torch.cuda.current_stream()
-    ev0.record(stream)
-    step_lat, agg = [], {}
-    for i in range(args.steps):
-        ts = time.perf_counter()
-        _, _, st = idx.query(batches[args.warmup + i], k, flags=qflags,
-                             out=(ids, dist_out), **qkw)
-        step_lat.append(time.perf_counter() - ts)
-        for key, v in st.items():
-            agg[key] = agg.get(key, 0) + v
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    t_dev, agg, step_lat = timed(qflags, args.steps, args.warmup, 0)
     clocks = sampler.stop()
-    t_dev = ev0.elapsed_time(ev1) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_dev], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(t.item())
     value = ws * B * args.steps / t_dev
 
     # end to end through the C ABI with host buffers (pinned queries in,
@@ -288,28 +301,57 @@ def main():
         e2e = dict(value=ws * B * args.steps / t_e2e, unit="queries/s",
                    h2d_bytes_per_step=B * n * 4, d2h_bytes_per_step=B * k * 12)
 
+    # the plain float32 path on the same index, for comparison
+    forms = {args.form: dict(value=value, ms_per_step=t_dev / args.steps * 1e3)}
+    plain = None
+    if args.form != "plain" and args.plain_steps > 0:
+        tp, aggp, _ = timed(binding.HK_Q_TIMING, args.plain_steps, 1, args.warmup)
+        forms["plain"] = dict(value=ws * B * args.plain_steps / tp, ms_per_step=tp / args.plain_steps * 1e3)
+        plain = aggp
+
     if rank != 0:
         return
     pk = peaks()
-    scan_s = agg["scan_ns"] / 1e9
-    flops = 3.0 * agg["points_computed"]
     alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-    alu_ach = flops / scan_s / 1e12 if scan_s else None
-    hbm_ach = agg["scan_bytes"] / scan_s / 1e9 if scan_s else None
-    alu_frac = alu_ach / alu_peak if alu_ach else 0
-    hbm_frac = hbm_ach / pk["hbm_gbs"] if hbm_ach else 0
-    if alu_frac >= hbm_frac:
-        roof = dict(bound="alu", achieved=alu_ach, peak=alu_peak, unit="TFLOP/s", frac=alu_frac,
-                    traffic=None, kernel="k_scan",
-                    peak_note="FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz; 3 flops per "
-                              "(q-x)^2 point" % pk["sm_max_mhz"],
-                    hbm_side=dict(achieved=hbm_ach, peak=pk["hbm_gbs"], unit="GB/s", frac=hbm_frac,
-                                  peak_source=pk["source"]))
+
+    def plain_roof(a):
+        scan_s = a["scan_ns"] / 1e9
+        alu_ach = 3.0 * a["points_computed"] / scan_s / 1e12 if scan_s else None
+        hbm_ach = a["scan_bytes"] / scan_s / 1e9 if scan_s else None
+        return dict(kernel="k_scan", alu=dict(achieved=alu_ach, peak=alu_peak, unit="TFLOP/s",
+                                              frac=(alu_ach or 0) / alu_peak),
+                    hbm=dict(achieved=hbm_ach, peak=pk["hbm_gbs"], unit="GB/s",
+                             frac=(hbm_ach or 0) / pk["hbm_gbs"]),
+                    share_of_step=None)
+
+    if args.form == "plain":
+        pr = plain_roof(agg)
+        if pr["alu"]["frac"] >= pr["hbm"]["frac"]:
+            roof = dict(bound="alu", achieved=pr["alu"]["achieved"], peak=alu_peak, unit="TFLOP/s",
+                        frac=pr["alu"]["frac"], traffic=None, kernel="k_scan",
+                        peak_note="derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz; "
+                                  "3 flops per (q-x)^2 point" % pk["sm_max_mhz"])
+        else:
+            roof = dict(bound="hbm", achieved=pr["hbm"]["achieved"], peak=pk["hbm_gbs"], unit="GB/s",
+                        frac=pr["hbm"]["frac"], traffic=None, kernel="k_scan",
+                        peak_note="of measured (%s)" % pk["source"])
+        roof["kernel_share_of_step"] = agg["scan_ns"] / 1e9 / t_dev
     else:
-        roof = dict(bound="hbm", achieved=hbm_ach, peak=pk["hbm_gbs"], unit="GB/s", frac=hbm_frac,
-                    traffic=None, kernel="k_scan", peak_source=pk["source"],
-                    alu_side=dict(achieved=alu_ach, peak=alu_peak, unit="TFLOP/s", frac=alu_frac))
-    roof["scan_share_of_step"] = scan_s / t_dev if t_dev else None
+        tc_s = agg["tc_ns"] / 1e9
+        flops = 2.0 * n * agg["tc_pairs"]
+        ach = flops / tc_s / 1e12 if tc_s else None
+        peak_t = pk.get("bf16_tflops_sustained") or 1713.1
+        roof = dict(bound="tensor", achieved=ach, peak=peak_t, unit="TFLOP/s", frac=(ach or 0) / peak_t,
+                    traffic=None, kernel="k_tc_scan",
+                    peak_note="of measured sustained bf16 (%s); %s dense rate equals bf16's nominally; "
+                              "2n flops per (query, series) pair" % (pk["source"], args.form),
+                    frac_of_burst=(ach or 0) / (pk.get("bf16_tflops") or 1920.7),
+                    hbm_side=dict(achieved=agg["tc_bytes"] / tc_s / 1e9 if tc_s else None,
+                                  peak=pk["hbm_gbs"], unit="GB/s",
+                                  note="16-bit rows + norms copied per query block (L2 serves repeats)"),
+                    kernel_share_of_step=tc_s / t_dev)
+        if plain:
+            roof["plain_k_scan"] = plain_roof(plain)
 
     cpu = None
     if sample is not None:
@@ -321,23 +363,30 @@ def main():
                           % (nqb, rows, dt, N))
 
     lat = sorted(step_lat)
+    dtype = {"plain": "f32", "bf16": "bf16", "fp16": "fp16"}[args.form]
     line = dict(
         metric="exact %d-NN queries/s (%s)" % (k, "%dM x %d" % (N // 1_000_000, n) if N >= 1_000_000 else "%d x %d" % (N, n)),
         value=value, unit="queries/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
         ms_per_step=t_dev / args.steps * 1e3, higher_is_better=True, scaling="weak",
-        vs_baseline=None, dtype="f32", data="synthetic",
+        vs_baseline=None, dtype=dtype, data="synthetic",
         config=dict(workload=wl["desc"], N=N, n=n, leaf_capacity=wl["tau"], k=k,
-                    queries_per_step=B, queries_total=wl["nq"], parallelism="replicas" if ws > 1 else "1 GPU",
+                    queries_per_step=B, queries_total=wl["nq"],
+                    form={"plain": "float32 scan", "bf16": "tensor cores, bfloat16 copy",
+                          "fp16": "tensor cores, float16 copy"}[args.form]
+                         + " + exact float32/binary64 rescore",
+                    parallelism="replicas" if ws > 1 else "1 GPU",
                     l2="inputs larger than L2 (%.0f GB collection)" % (N * n * 4 / 1e9)),
         latency_ms=dict(kind="batch completion (closed loop, %d queries per batch)" % B,
                         p50=lat[len(lat) // 2] * 1e3, p99=lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3),
         clocks=clocks, e2e=e2e, gpu_launches=agg["kernel_launches"], roofline=roof,
-        cpu_baseline=cpu,
+        cpu_baseline=cpu, forms=forms,
         pruning=dict(leaves_candidate_frac=agg["leaves_candidate"] / max(1, agg["leaves_total"]),
                      series_candidate=agg["series_candidate"], sax_pruned=agg["series_sax_pruned"],
                      abandoned=agg["series_abandoned"], full=agg["series_full"],
-                     points=agg["points_computed"], rescored=agg["rescored"],
-                     fallback=agg["fallback_queries"], skip_sequential=agg["skip_sequential"]),
+                     points=agg["points_computed"], tc_pairs=agg["tc_pairs"],
+                     tc_candidates=agg["tc_candidates"], rescored=agg["rescored"],
+                     retried=agg["retried_queries"], fallback=agg["fallback_queries"],
+                     skip_sequential=agg["skip_sequential"]),
         index=dict(build_s=t_build, gen_s=t_gen, leaves=info["leaves"], depth=info["depth"],
                    max_segments=info["max_segments"]),
     )

@@ -131,12 +131,15 @@ typedef struct {
                                      after a candidate list or pool overflowed  */
     int64_t work_items;           /* scan work items launched                    */
     int64_t skip_sequential;      /* queries scanned without LB_SAX (EAPCA_TH)   */
-    int64_t scan_ns;              /* scan kernel time (HK_Q_TIMING), ns          */
+    int64_t scan_ns;              /* float32 scan kernel time (HK_Q_TIMING), ns  */
     int64_t kernel_launches;      /* kernels this call launched                  */
     int64_t scan_bytes;           /* series bytes the scan read: 64 B per 16-point
                                      chunk loaded + 16 B per iSAX word, per item */
     int64_t tc_pairs;             /* (query, series) distances on tensor cores   */
     int64_t tc_candidates;        /* of those, kept for the exact rescore        */
+    int64_t tc_ns;                /* tensor-core kernel time (HK_Q_TIMING), ns   */
+    int64_t tc_bytes;             /* 16-bit rows and norms the tensor-core kernel
+                                     copied in (per query block)                 */
 } hk_query_stats;
 
 /*

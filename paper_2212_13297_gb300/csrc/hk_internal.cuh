@@ -242,7 +242,7 @@ struct TcArgs {
     int32_t *qflag;
     int32_t *err;
     long long *stats;
-    int stat_pairs, stat_cands;
+    int stat_pairs, stat_cands, stat_bytes;
     uint32_t idesc;
     float *dbg_lo, *dbg_up;      // if set: certified interval of every pair, [q * N + pos]
     int64_t N;

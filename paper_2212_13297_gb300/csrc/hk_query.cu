@@ -54,7 +54,7 @@ enum StatIdx {
     ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_APPROX, ST_LEAVES_CAND, ST_SERIES_CAND,
     ST_SAX_PRUNED, ST_ABANDONED, ST_FULL, ST_POINTS, ST_RESCORED, ST_FALLBACK,
     ST_ITEMS, ST_SKIPSEQ, ST_SCAN_NS, ST_LAUNCHES, ST_SCAN_BYTES, ST_RETRIED, ST_TC_PAIRS,
-    ST_TC_CANDS
+    ST_TC_CANDS, ST_TC_BYTES
 };
 
 struct ScanArgs {
@@ -988,6 +988,7 @@ void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s, Scan
     stats->retried_queries = st[ST_RETRIED];
     stats->tc_pairs = st[ST_TC_PAIRS];
     stats->tc_candidates = st[ST_TC_CANDS];
+    stats->tc_bytes = st[ST_TC_BYTES];
     stats->scan_ns = timer ? timer->total_ns() : 0;
     stats->kernel_launches = launches;
 }
@@ -1023,8 +1024,8 @@ namespace {
 // U_init: initial bounds (device, float bits) or nullptr for +inf; with
 // bounds given, the approximate search is skipped.
 void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, const hk_query_opts &o,
-                cudaStream_t s, const uint32_t *U_init, ScanTimer *timer, std::vector<int32_t> &flags,
-                std::vector<uint32_t> &Uh) {
+                cudaStream_t s, const uint32_t *U_init, ScanTimer *timer, ScanTimer *tctimer,
+                std::vector<int32_t> &flags, std::vector<uint32_t> &Uh) {
     const int n = idx->n;
     const int64_t L = idx->L;
     const float rho = rho_for(n);
@@ -1183,13 +1184,14 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         t.stats = (long long *)ws.stats.p;
         t.stat_pairs = ST_TC_PAIRS;
         t.stat_cands = ST_TC_CANDS;
+        t.stat_bytes = ST_TC_BYTES;
         t.idesc = tc_idesc(idx->fmt16);
         t.dbg_lo = nullptr;
         t.dbg_up = nullptr;
         t.N = idx->N;
-        if (timer) timer->mark(s);
+        if (tctimer) tctimer->mark(s);
         launch_tc_scan(t, s);
-        if (timer) timer->mark(s);
+        if (tctimer) tctimer->mark(s);
         k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
         HK_CHECK_LAUNCH();
         launch_tc_rescore(Qd, v.X, n, nq, ws.cand_cnt.p, ws.cand_p.p, ws.cand_lb.p, cand_C, ws.U.p,
@@ -1215,11 +1217,11 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
                int64_t *out_ids, float *out_dist, hk_query_stats *stats) {
     Workspace &ws = idx->ws;
     const long long launches0 = g_launches;
-    ScanTimer timer;
-    timer.on = (o.flags & HK_Q_TIMING) != 0;
+    ScanTimer timer, tctimer;
+    timer.on = tctimer.on = (o.flags & HK_Q_TIMING) != 0;
     std::vector<int32_t> flags;
     std::vector<uint32_t> Uh;
-    query_pass(idx, ws, Qd, nq, k, o, s, nullptr, &timer, flags, Uh);
+    query_pass(idx, ws, Qd, nq, k, o, s, nullptr, &timer, &tctimer, flags, Uh);
 
     // Queries whose lists or pool overflowed: run them again starting from
     // their final bound, which is tight, so far fewer candidates qualify.
@@ -1241,7 +1243,7 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
         // near-ties that crowd the precision form's wider band fit its lists
         hk_query_opts o2 = o;
         o2.flags &= ~HK_Q_BF16;
-        query_pass(idx, w2, w2.Q.p, nsub, k, o2, s, w2.Uinit.p, &timer, flags2, U2);
+        query_pass(idx, w2, w2.Q.p, nsub, k, o2, s, w2.Uinit.p, &timer, &tctimer, flags2, U2);
         LeafView v;
         v.X = idx->X.p;
         v.perm = idx->perm.p;
@@ -1273,6 +1275,7 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
     copy_out(ws, nq, k, out_ids, out_dist, s);
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
     copy_stats(ws, stats, s, &timer, g_launches - launches0);
+    if (stats) stats->tc_ns = tctimer.total_ns();
 }
 
 void run_scan(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k, cudaStream_t s,

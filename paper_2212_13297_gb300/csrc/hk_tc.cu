@@ -28,14 +28,14 @@
 // (next 8 points), stride-dimension offset (n/8)*128 bytes (next 8 series).
 // The query block is gathered into the same layout with ordinary stores.
 //
-// CTA roles (10 warps): warp 0 issues the bulk copies (series tile and the
-// tile's norm pairs), warp 1 (one thread) issues tcgen05.mma and
+// CTA roles (10 warps): warp 0 issues the bulk copies (series tiles by
+// K-chunks, and the tile's norm pairs), warp 1 (one thread) issues tcgen05.mma and
 // tcgen05.commit, warps 2-9 read the accumulators with tcgen05.ld and filter:
 // warp w reads TMEM lane quarter w%4 (query rows 32(w%4)..+31) and half of
 // the tile's columns.  Per element the filter is two FMAs and a compare
 // against a per-row threshold; the exact bounds are formed only for the
 // rare survivors.
-// Two shared-memory stages for series tiles, two TMEM accumulators.  Every
+// Sixteen shared-memory chunk stages for series tiles, two TMEM accumulators.  Every
 // mbarrier wait is bounded; on a timeout the CTA raises an error flag,
 // drains, frees its tensor memory and stops.
 #include <cuda_bf16.h>
@@ -48,11 +48,16 @@ namespace {
 
 constexpr int kTcM = 128;        // queries per block (MMA M)
 constexpr int kTcN = 128;        // series per tile (MMA N)
+// Series tiles (128 series, 16 groups of 8: one contiguous run in the
+// core-matrix layout) stream through kTcStages shared-memory stages, one
+// bulk copy each.
 constexpr int kTcStages = 2;
-// Norm slots: tile g uses slot g % 4.  The producer writes tile g's slot
-// only after the MMA of tile g-2 completed, which itself waited for the
-// epilogue of tile g-4, the slot's previous user.
-constexpr int kNormSlots = 4;
+constexpr int kTcStageBytes = kTcN * 256 * 2;   // longest series (256 points)
+// Norm slots: tile g uses slot g % 8.  The producer is at most kTcStages
+// tiles ahead of the MMA, which is at most 2 ahead of the epilogue: when the
+// producer writes tile g's norms, tile g-8 (the slot's previous user) was
+// read long before.
+constexpr int kNormSlots = 8;
 constexpr int kTcEpiWarps = 8;   // two per TMEM lane quarter, each half the columns
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTmemCols = 256;   // two accumulators of kTcN columns
@@ -198,10 +203,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     const int n = A.n;
     const uint32_t a_bytes = (uint32_t)kTcM * n * 2;
-    const uint32_t b_bytes = (uint32_t)kTcN * n * 2;
+    const uint32_t b_bytes = (uint32_t)kTcN * n * 2;             // a whole tile
+    const int nst = kTcStages;
     unsigned char *sA = tc_smem;                             // 1024-aligned
     unsigned char *sB = tc_smem + a_bytes;                   // stages follow
-    float2 *sX = reinterpret_cast<float2 *>(sB + kTcStages * b_bytes);     // kNormSlots * kTcN
+    float2 *sX = reinterpret_cast<float2 *>(sB + kTcStages * kTcStageBytes);  // kNormSlots * kTcN
     float *kbest = reinterpret_cast<float *>(sX + kNormSlots * kTcN);      // kTcM * kLocalK
     TcShared &S = *reinterpret_cast<TcShared *>(kbest + kTcM * kLocalK);
 
@@ -230,12 +236,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     tc_fence_after();
     const uint32_t tmem = S.tmem_base;
     const int64_t total = A.item_off[A.L];
-    const int ksteps = n / 16;
-    const uint32_t lbo = 128, sbo = (uint32_t)(n / 8) * 128;
+    const uint32_t lbo = 128, sbo = (uint32_t)(n / 8) * 128;   // A: full K resident
 
     // running counts of barrier completions (phases), kept per role
     uint32_t g_tile = 0;   // tiles processed by this CTA so far (all roles agree)
-    long long my_cand = 0, my_pairs = 0;
+    long long my_cand = 0, my_pairs = 0, my_bytes = 0;
 
     for (;;) {
         if (tid == 0) S.item = atomicAdd(A.work_ctr, 1);
@@ -260,51 +265,56 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
             for (int g = 0; g < kTcM; ++g) S.qid[g] = g < S.gq ? lq[g] : -1;
         }
         __syncthreads();
-        // gather the query block into the core-matrix layout (zeros past gq)
+        // gather the query block into the core-matrix layout (zeros past gq);
+        // consecutive threads fill consecutive 16-byte rows of a core matrix
         {
-            const int chunks = kTcM * (n / 8);   // 16-byte pieces
+            const int kc = n / 8;
+            const int chunks = kTcM * kc;   // 16-byte pieces
             for (int c = tid; c < chunks; c += kTcThreads) {
-                const int r = c / (n / 8), k8 = c % (n / 8);
+                const int rr = c & 7, k8 = (c >> 3) % kc, r8 = (c >> 3) / kc;
+                const int r = r8 * 8 + rr;
                 uint4 v = make_uint4(0, 0, 0, 0);
                 const int q = S.qid[r];
                 if (q >= 0) v = *reinterpret_cast<const uint4 *>(A.Qb + (int64_t)q * n + k8 * 8);
-                *reinterpret_cast<uint4 *>(sA + ((r >> 3) * (n / 8) + k8) * 128 + (r & 7) * 16) = v;
+                *reinterpret_cast<uint4 *>(sA + (r8 * kc + k8) * 128 + rr * 16) = v;
             }
             fence_proxy_async();
         }
         __syncthreads();
         const int T = S.tiles;
         const int64_t base = S.base, s0 = S.s0, s1 = S.s1;
+        if (tid == 0) my_bytes += (long long)T * (b_bytes + kTcN * (long long)sizeof(float2));
 
         if (warp == 0) {
-            // ---------------- producer: one bulk copy per tile
+            // ---------------- producer: one bulk copy per tile, plus its norms
             if (lane == 0) {
                 for (int t = 0; t < T; ++t) {
                     const uint32_t gt = g_tile + t;
-                    const int s = gt % kTcStages;
-                    const uint32_t use = gt / kTcStages;
+                    const int s = gt % nst;
+                    const uint32_t use = gt / nst;
                     if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1, &S.abort_flag)) break;
                     const int64_t row0 = base + (int64_t)t * kTcN;
-                    mbar_arrive_expect_tx(&S.full[s], b_bytes + kTcN * (uint32_t)sizeof(float2));
-                    bulk_g2s(sB + s * b_bytes, A.Xb + row0 * n, b_bytes, &S.full[s]);
-                    bulk_g2s(sX + (gt % kNormSlots) * kTcN, A.xq + row0, kTcN * (uint32_t)sizeof(float2),
-                             &S.full[s]);
+                    const uint32_t norm_bytes = kTcN * (uint32_t)sizeof(float2);
+                    mbar_arrive_expect_tx(&S.full[s], b_bytes + norm_bytes);
+                    bulk_g2s(sB + s * kTcStageBytes, A.Xb + row0 * n, b_bytes, &S.full[s]);
+                    bulk_g2s(sX + (gt % kNormSlots) * kTcN, A.xq + row0, norm_bytes, &S.full[s]);
                 }
             }
         } else if (warp == 1) {
             // ---------------- MMA issuer
             if (lane == 0) {
                 const uint32_t a_base = smem_u32(sA);
+                const int ksteps = n / 16;
                 for (int t = 0; t < T; ++t) {
                     const uint32_t gt = g_tile + t;
-                    const int s = gt % kTcStages;
-                    const uint32_t use = gt / kTcStages;
+                    const int s = gt % nst;
+                    const uint32_t use = gt / nst;
                     const int b = gt & 1;
                     const uint32_t ause = gt >> 1;
                     if (ause > 0 && !mbar_wait(&S.acc_empty[b], (ause - 1) & 1, &S.abort_flag)) break;
                     if (!mbar_wait(&S.full[s], use & 1, &S.abort_flag)) break;
                     tc_fence_after();
-                    const uint32_t b_base = smem_u32(sB + s * b_bytes);
+                    const uint32_t b_base = smem_u32(sB + s * kTcStageBytes);
                     const uint32_t d = tmem + (uint32_t)(b * kTcN);
                     for (int ks = 0; ks < ksteps; ++ks) {
                         const uint64_t ad = smem_desc(a_base + ks * 2 * 128, lbo, sbo);
@@ -327,11 +337,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                 qoff2 = A.qoff2[q];
                 U = __uint_as_float(A.U[q]);
             }
-            float *kb = kbest + r * kLocalK;
-            // both halves of a row share its list; each keeps its own slots
+            // the k best upper bounds of this thread: slot i of epilogue thread
+            // e at kbest[i * 256 + e] (conflict-free); the two column halves
+            // of a row keep separate lists
+            float *kb = kbest + (tid - 64);
             const int kl = (A.k <= kLocalK / 2) ? A.k : 0;
-            kb += half * (kLocalK / 2);
-            for (int i = 0; i < kl; ++i) kb[i] = INFINITY;
+            for (int i = 0; i < kl; ++i) kb[i * 256] = INFINITY;
             float kth = INFINITY;      // k-th smallest upper bound seen by this thread
             long long pairs = 0;
             for (int t = 0; t < T; ++t) {
@@ -341,7 +352,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                 const uint32_t ause = gt >> 1;
                 if (!mbar_wait_warp(&S.acc_full[b], ause & 1, &S.abort_flag)) break;
                 tc_fence_after();
-                if (q >= 0) U = fminf(U, __uint_as_float(A.U[q]));
+                if (q >= 0 && (t & 7) == 0) U = fminf(U, __uint_as_float(A.U[q]));
                 const int64_t row0 = base + (int64_t)t * kTcN;
                 // columns of this tile inside [s0, s1)
                 const int jlo = (int)max((int64_t)0, s0 - row0);
@@ -389,10 +400,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                         const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
                         if (kl && up < kth) {
                             int m = 0;
-                            for (int i = 1; i < kl; ++i) if (kb[i] > kb[m]) m = i;
-                            kb[m] = up;
+                            for (int i = 1; i < kl; ++i) if (kb[i * 256] > kb[m * 256]) m = i;
+                            kb[m * 256] = up;
                             float mx = kb[0];
-                            for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i]);
+                            for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i * 256]);
                             kth = mx;
                         }
                         if (lo <= U) {
@@ -442,6 +453,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     if (lane == 0 && A.stats) {
         stat_add(&A.stats[A.stat_pairs], my_pairs);
         stat_add(&A.stats[A.stat_cands], my_cand);
+        if (tid == 0) stat_add(&A.stats[A.stat_bytes], my_bytes);
     }
 }
 
@@ -560,7 +572,7 @@ __global__ void k_tc_rescore(const float *__restrict__ Q, const float *__restric
 }
 
 size_t tc_smem_bytes(int n) {
-    return (size_t)kTcM * n * 2 + (size_t)kTcStages * kTcN * n * 2 + (size_t)kNormSlots * kTcN * 8 +
+    return (size_t)kTcM * n * 2 + (size_t)kTcStages * kTcStageBytes + (size_t)kNormSlots * kTcN * 8 +
            (size_t)kTcM * kLocalK * 4 + sizeof(TcShared) + 1024;
 }
 
