@@ -178,6 +178,65 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def serve(binding, idx, Q_all, k, max_batch, qflags, args):
+    """Open-loop serving: requests arrive one query at a time (Poisson, rate
+    args.serve) and are answered by the continuous-batching server; reports
+    arrival-to-answer latency and the rate at which answers came back."""
+    import threading
+    import numpy as np
+    Qh = Q_all.cpu().numpy()
+    rng = np.random.default_rng(11)
+    n_req = max(1, int(args.serve * args.serve_seconds))
+    gaps = rng.exponential(1.0 / args.serve, n_req)
+    sv = binding.Server(max_batch=max_batch, max_wait_us=0, query_flags=qflags, workers=2)
+    coll = sv.add(idx)
+    # warm the workers' buffers
+    for t in [sv.submit(coll, Qh[i], k) for i in range(min(64, len(Qh)))]:
+        sv.poll(t, k, timeout_us=60_000_000)
+    tickets = [None] * n_req
+    ready = threading.Semaphore(0)
+    lat = np.zeros(n_req)
+    t_done = [0.0]
+
+    def submitter():
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(n_req):
+            due += gaps[i]
+            d = due - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = sv.submit(coll, Qh[i % len(Qh)], k)
+            ready.release()
+
+    def poller():
+        for i in range(n_req):
+            ready.acquire()
+            r = None
+            while r is None:
+                r = sv.poll(tickets[i], k, timeout_us=10_000_000)
+            lat[i] = r[2] / 1e9
+        t_done[0] = time.perf_counter()
+
+    t_start = time.perf_counter()
+    ths = [threading.Thread(target=submitter), threading.Thread(target=poller)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    wall = t_done[0] - t_start
+    st = sv.stats()
+    sv.close()
+    ls = np.sort(lat)
+    return dict(kind="open loop, Poisson arrivals, one query per request, 2 workers",
+                offered_rate=args.serve, requests=n_req, answered_per_s=n_req / wall,
+                latency_ms=dict(p50=float(ls[n_req // 2]) * 1e3,
+                                p99=float(ls[min(n_req - 1, int(0.99 * n_req))]) * 1e3,
+                                max=float(ls[-1]) * 1e3),
+                batches=st["batches"], mean_batch=st["served"] / max(1, st["batches"]),
+                max_batch=st["max_batch"], errors=st["errors"])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -195,6 +254,10 @@ def main():
                     help="steps of the float32 path measured beside a tensor-core form")
     ap.add_argument("--form", default="fp16", choices=["plain", "bf16", "fp16"],
                     help="plain float32 scan, or the tensor-core form on a bfloat16 / float16 copy")
+    ap.add_argument("--serve", type=float, default=0.0,
+                    help="also drive the continuous-batching server with Poisson arrivals at this "
+                         "rate (requests/s) and report arrival-to-answer latency")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
@@ -309,6 +372,9 @@ def main():
         forms["plain"] = dict(value=ws * B * args.plain_steps / tp, ms_per_step=tp / args.plain_steps * 1e3)
         plain = aggp
 
+    serving = serve(binding, idx, Q_all, k, B, qflags & ~binding.HK_Q_TIMING, args) \
+        if args.serve > 0 else None
+
     if rank != 0:
         return
     pk = peaks()
@@ -379,7 +445,7 @@ def main():
         latency_ms=dict(kind="batch completion (closed loop, %d queries per batch)" % B,
                         p50=lat[len(lat) // 2] * 1e3, p99=lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3),
         clocks=clocks, e2e=e2e, gpu_launches=agg["kernel_launches"], roofline=roof,
-        cpu_baseline=cpu, forms=forms,
+        cpu_baseline=cpu, forms=forms, serving=serving,
         pruning=dict(leaves_candidate_frac=agg["leaves_candidate"] / max(1, agg["leaves_total"]),
                      series_candidate=agg["series_candidate"], sax_pruned=agg["series_sax_pruned"],
                      abandoned=agg["series_abandoned"], full=agg["series_full"],

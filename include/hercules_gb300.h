@@ -192,6 +192,57 @@ int hk_scan_knn_noalloc(const float *X, int64_t N, int32_t n, const float *Q,
                         int32_t nq, int32_t k, void *stream, int64_t *out_ids,
                         float *out_dist);
 
+/* ---- serving: continuous batching --------------------------------------------- */
+
+typedef struct hk_server hk_server;
+
+typedef struct {
+    int32_t max_batch;     /* most requests answered by one batch; 0 = 1024     */
+    int32_t max_wait_us;   /* how long a worker lingers to fill a batch once a
+                              request is pending; 0 = take what is pending      */
+    int64_t hbm_budget;    /* device bytes the workers' query work spaces may
+                              use in total; the batch size is capped to fit;
+                              0 = no cap                                        */
+    uint32_t query_flags;  /* HK_Q_* applied to every batch (HK_Q_BF16 uses the
+                              tensor-core form where the index has a copy)     */
+    int32_t workers;       /* concurrent batches (threads, CUDA streams); 0 = 2 */
+} hk_server_opts;
+
+typedef struct {
+    int64_t batches;       /* batches answered                                  */
+    int64_t served;        /* requests answered                                 */
+    int64_t max_batch;     /* largest batch so far                              */
+    int64_t errors;        /* batches that failed                               */
+    int64_t pending;       /* requests waiting for a batch                      */
+    int64_t busy_ns;       /* summed wall time of the batches                   */
+} hk_server_stats;
+
+/*
+ * A server answers exact k-NN requests against registered indexes by
+ * continuous batching (Sec. 4.1: queries arrive asynchronously): each worker
+ * takes the pending requests of one collection and answers them as one batch
+ * with k = the batch's largest k; each request receives the first k_i entries,
+ * which equal what hk_query returns for it alone.  Requests arriving while
+ * batches run join the next batch.  The server does not own the indexes;
+ * they must outlive it.  hk_server_destroy must not race with other calls on
+ * the same server.
+ */
+int hk_server_create(const hk_server_opts *opts, hk_server **out);
+int hk_server_add(hk_server *sv, hk_index *idx, int32_t *coll_id);
+/* q: host pointer to n floats (copied before return); k <= min(N, 1024). */
+int hk_submit(hk_server *sv, int32_t coll_id, const float *q, int32_t k,
+              uint64_t *ticket);
+/*
+ * Wait up to timeout_us for the request; on HK_OK the k ids / float32
+ * distances are written (host pointers) and the ticket is released; on
+ * HK_ETIMEOUT the ticket stays valid.  latency_ns (may be NULL): time from
+ * hk_submit to the batch's completion.
+ */
+int hk_poll(hk_server *sv, uint64_t ticket, int64_t *ids, float *dist,
+            int32_t timeout_us, int64_t *latency_ns);
+int hk_server_stats_get(hk_server *sv, hk_server_stats *out);
+int hk_server_destroy(hk_server *sv);
+
 /*
  * hk_isax_breakpoints -- the 255 iSAX breakpoints the library uses
  * (Sec. 2: alphabet 256; beta_j the standard normal quantile of j/256),

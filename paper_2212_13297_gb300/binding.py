@@ -63,6 +63,17 @@ class hk_index_info(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class hk_server_opts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_int64), ("query_flags", ctypes.c_uint32),
+                ("workers", ctypes.c_int32)]
+
+
+class hk_server_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "batches", "served", "max_batch", "errors", "pending", "busy_ns")]
+
+
 class HerculesError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("hercules error %d: %s" % (code, msg))
@@ -75,7 +86,8 @@ _lib = None
 EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_scan_knn",
            "hk_scan_knn_noalloc",
            "hk_isax_breakpoints", "hk_index_export", "hk_debug_lb_eapca", "hk_debug_lb_sax",
-           "hk_debug_tc_dist",
+           "hk_debug_tc_dist", "hk_server_create", "hk_server_add", "hk_submit", "hk_poll",
+           "hk_server_stats_get", "hk_server_destroy",
            "hk_last_error", "hk_version"]
 
 
@@ -105,6 +117,14 @@ def lib():
         L.hk_debug_lb_eapca.argtypes = [vp, vp, ctypes.c_int32, vp]
         L.hk_debug_lb_sax.argtypes = [vp, vp, ctypes.c_int32, vp]
         L.hk_debug_tc_dist.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
+        L.hk_server_create.argtypes = [ctypes.POINTER(hk_server_opts), ctypes.POINTER(vp)]
+        L.hk_server_add.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+        L.hk_submit.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int32,
+                                ctypes.POINTER(ctypes.c_uint64)]
+        L.hk_poll.argtypes = [vp, ctypes.c_uint64, vp, vp, ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_int64)]
+        L.hk_server_stats_get.argtypes = [vp, ctypes.POINTER(hk_server_stats)]
+        L.hk_server_destroy.argtypes = [vp]
         L.hk_last_error.restype = ctypes.c_char_p
         L.hk_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -251,3 +271,55 @@ def scan_knn(X, Q, k: int, stream=None):
     _check(lib().hk_scan_knn(_ptr(X), N, n, _ptr(Q), nq, int(k), _stream(stream), _ptr(ids),
                              _ptr(dist)))
     return ids, dist
+
+
+class Server:
+    """Continuous-batching server over registered indexes (hk_server_*)."""
+
+    def __init__(self, max_batch=0, max_wait_us=0, hbm_budget=0, query_flags=0, workers=0):
+        o = hk_server_opts(int(max_batch), int(max_wait_us), int(hbm_budget), int(query_flags),
+                           int(workers))
+        h = ctypes.c_void_p()
+        _check(lib().hk_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._n = {}
+
+    def add(self, index):
+        c = ctypes.c_int32()
+        _check(lib().hk_server_add(self._h, index._h, ctypes.byref(c)))
+        self._n[c.value] = index.n
+        return c.value
+
+    def submit(self, coll, q, k):
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        t = ctypes.c_uint64()
+        _check(lib().hk_submit(self._h, int(coll), _ptr(q), int(k), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket, k, timeout_us=1_000_000):
+        """(ids, dist, latency_ns), or None if not done within the timeout."""
+        ids = np.empty(k, np.int64)
+        dist = np.empty(k, np.float32)
+        lat = ctypes.c_int64()
+        rc = lib().hk_poll(self._h, ctypes.c_uint64(ticket), _ptr(ids), _ptr(dist),
+                           int(timeout_us), ctypes.byref(lat))
+        if rc == HK_ETIMEOUT:
+            return None
+        _check(rc)
+        return ids, dist, lat.value
+
+    def stats(self):
+        st = hk_server_stats()
+        _check(lib().hk_server_stats_get(self._h, ctypes.byref(st)))
+        return {f[0]: getattr(st, f[0]) for f in st._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hk_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -186,6 +186,10 @@ void build_index(hk_index *idx, const float *X, int64_t N, int n, const hk_build
 void run_query(hk_index *idx, const float *Qdev, int nq, int k, const hk_query_opts &o,
                cudaStream_t s, int64_t *out_ids_host_or_dev, float *out_dist_host_or_dev,
                hk_query_stats *stats);
+// The same with caller-owned work spaces (one pair per concurrent caller).
+void run_query_ws(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float *Qdev, int nq, int k,
+                  const hk_query_opts &o, cudaStream_t s, int64_t *out_ids, float *out_dist,
+                  hk_query_stats *stats);
 void run_scan(const float *Xdev, int64_t N, int n, const float *Qdev, int nq, int k,
               cudaStream_t s, int64_t *out_ids, float *out_dist);
 void debug_lb_eapca(hk_index *idx, const float *Qdev, int nq, double *out_host);

@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -786,12 +787,11 @@ ScanConfig choose_scan(int n, int k, bool sax, int want_G) {
 
 template <int G>
 void launch_scan_g(const ScanArgs &a, size_t smem, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         HK_CHECK_CUDA(cudaFuncSetAttribute(k_scan<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            200 * 1024));
-        configured = true;
-    }
+    });
     int per_sm = 0;
     HK_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<G>, kBT, smem));
     if (per_sm < 1) per_sm = 1;
@@ -1215,7 +1215,12 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
 
 void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opts &o, cudaStream_t s,
                int64_t *out_ids, float *out_dist, hk_query_stats *stats) {
-    Workspace &ws = idx->ws;
+    run_query_ws(idx, idx->ws, idx->ws_retry, Qd, nq, k, o, s, out_ids, out_dist, stats);
+}
+
+void run_query_ws(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float *Qd, int nq, int k,
+                  const hk_query_opts &o, cudaStream_t s, int64_t *out_ids, float *out_dist,
+                  hk_query_stats *stats) {
     const long long launches0 = g_launches;
     ScanTimer timer, tctimer;
     timer.on = tctimer.on = (o.flags & HK_Q_TIMING) != 0;
@@ -1230,7 +1235,7 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
         if (flags[q] & 1) sel.push_back(q);
     if (!sel.empty()) {
         const int nsub = (int)sel.size();
-        Workspace &w2 = idx->ws_retry;
+        Workspace &w2 = ws_retry;
         w2.Q.reserve((size_t)nsub * idx->n, s);
         w2.Uinit.reserve(nsub, s);
         w2.sel.reserve(nsub, s);

@@ -40,6 +40,8 @@
 // drains, frees its tensor memory and stops.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "hk_device.cuh"
 #include "hk_internal.cuh"
 
@@ -598,12 +600,11 @@ double tc_error_coefficient(int n, int fmt) {
 
 void launch_tc_scan(const TcArgs &a, cudaStream_t s) {
     const size_t smem = tc_smem_bytes(a.n);
-    static bool configured = false;
-    if (!configured) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         HK_CHECK_CUDA(cudaFuncSetAttribute(k_tc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)tc_smem_bytes(256)));
-        configured = true;
-    }
+    });
     int dev = 0, sms = 0;
     HK_CHECK_CUDA(cudaGetDevice(&dev));
     HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

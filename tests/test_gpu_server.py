@@ -1,0 +1,124 @@
+"""The continuous-batching server: every request's answer equals the answer
+of the same query alone (hk_query, and the brute-force oracle), whatever
+batch it was answered in; bounded waits; argument checks."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hb():
+    from paper_2212_13297_gb300 import build, binding
+    build.build()
+    binding.lib()
+    assert torch.cuda.is_available(), "GPU test without a GPU"
+    return binding
+
+
+@pytest.fixture(scope="module")
+def two_collections(hb):
+    from paper_2212_13297_gb300 import workload as wl
+    X1 = wl.random_walk(30_000, 64, seed=101, device="cuda")
+    X2 = wl.gaussian(20_000, 128, seed=102, device="cuda", l2=True)
+    i1 = hb.Index(X1, 300)
+    i2 = hb.Index(X2, 300, flags=hb.HK_BUILD_FP16)
+    Q1, _ = wl.queries(X1, 120, [0.05, 0.5, 1.0], seed=103)
+    Q2, _ = wl.queries(X2, 80, [0.01, 0.1], seed=104, norm="l2")
+    return dict(X=[X1, X2], idx=[i1, i2], Q=[Q1.cpu().numpy(), Q2.cpu().numpy()])
+
+
+@pytest.mark.parametrize("flags", [0, "bf16"])
+def test_mixed_requests_equal_their_answers_alone(hb, oracle_lib, two_collections, flags):
+    c = two_collections
+    qflags = hb.HK_Q_BF16 if flags == "bf16" else 0
+    sv = hb.Server(max_batch=64, max_wait_us=200, query_flags=qflags, workers=2)
+    coll = [sv.add(c["idx"][0]), sv.add(c["idx"][1])]
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(120):
+        reqs.append((0, i, int(rng.choice([1, 5, 20]))))
+    for i in range(80):
+        reqs.append((1, i, int(rng.choice([1, 10]))))
+    rng.shuffle(reqs)
+    tickets = [None] * len(reqs)
+
+    def submit(part):
+        for j in part:
+            cidx, qi, k = reqs[j]
+            tickets[j] = sv.submit(coll[cidx], c["Q"][cidx][qi], k)
+
+    ths = [threading.Thread(target=submit, args=(range(p, len(reqs), 2),)) for p in range(2)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    got = []
+    for j, (cidx, qi, k) in enumerate(reqs):
+        r = sv.poll(tickets[j], k, timeout_us=30_000_000)
+        assert r is not None
+        got.append(r)
+    st = sv.stats()
+    assert st["served"] == len(reqs) and st["errors"] == 0 and st["pending"] == 0
+    assert st["batches"] < len(reqs)          # requests were batched
+    sv.close()
+    # alone: the same query through hk_query
+    for j, (cidx, qi, k) in enumerate(reqs):
+        ids, dist, _ = c["idx"][cidx].query(c["Q"][cidx][qi:qi + 1], k)
+        np.testing.assert_array_equal(got[j][0], ids[0])
+        np.testing.assert_array_equal(got[j][1], dist[0])
+    # and a sample against the oracle
+    for cidx in (0, 1):
+        Xh = c["X"][cidx].cpu().numpy()
+        qs = [j for j, r in enumerate(reqs) if r[0] == cidx][:12]
+        for j in qs:
+            _, qi, k = reqs[j]
+            oids, _ = oracle.knn(Xh, c["Q"][cidx][qi:qi + 1], k)
+            np.testing.assert_array_equal(got[j][0], oids[0])
+
+
+def test_poll_timeout_and_budget_cap(hb, two_collections):
+    c = two_collections
+    # a worker that lingers 300 ms for more requests: a 1 ms poll times out
+    sv = hb.Server(max_batch=512, max_wait_us=300_000, workers=1)
+    coll = sv.add(c["idx"][0])
+    t = sv.submit(coll, c["Q"][0][0], 5)
+    assert sv.poll(t, 5, timeout_us=1000) is None
+    r = sv.poll(t, 5, timeout_us=10_000_000)
+    assert r is not None and r[2] > 0
+    sv.close()
+    # a device budget that fits only a few queries caps the batch size
+    sv = hb.Server(max_batch=512, max_wait_us=50_000, hbm_budget=64 << 20, workers=1)
+    coll = sv.add(c["idx"][0])
+    ts = [sv.submit(coll, c["Q"][0][i], 3) for i in range(60)]
+    for i, t in enumerate(ts):
+        ids, _, _ = sv.poll(t, 3, timeout_us=30_000_000)
+        ref, _, _ = c["idx"][0].query(c["Q"][0][i:i + 1], 3)
+        np.testing.assert_array_equal(ids, ref[0])
+    st = sv.stats()
+    assert st["max_batch"] < 60
+    sv.close()
+
+
+def test_server_rejects_bad_requests(hb, two_collections):
+    c = two_collections
+    sv = hb.Server(workers=1)
+    coll = sv.add(c["idx"][0])
+    q = c["Q"][0][0].copy()
+    q[3] = np.nan
+    with pytest.raises(hb.HerculesError) as e:
+        sv.submit(coll, q, 1)
+    assert e.value.code == hb.HK_EINVAL
+    with pytest.raises(hb.HerculesError):
+        sv.submit(coll + 5, c["Q"][0][0], 1)
+    with pytest.raises(hb.HerculesError):
+        sv.submit(coll, c["Q"][0][0], 2000)
+    with pytest.raises(hb.HerculesError):
+        sv.poll(987654, 1, timeout_us=10)
+    sv.close()
