@@ -168,8 +168,9 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                      smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// Issue one 32-column TMEM load (lanes of this warp's quarter); the values
+// are valid only after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -180,9 +181,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 struct TcShared {
@@ -363,59 +364,86 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                 const float2 *xs = sX + (gt % kNormSlots) * kTcN;
                 const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
                                        (uint32_t)(b * kTcN + half * (kTcN / 2));
-                for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
-                    float v[32];
-                    tmem_ld32(taddr + c0, v);
-                    if (q < 0) continue;
-                    const int cb = half * (kTcN / 2) + c0;
-                    // columns of this chunk inside [s0, s1)
-                    const int a = max(jlo - cb, 0), z = min(jhi - cb, 32);
-                    if (a >= z) continue;
-                    const uint32_t valid = (z >= 32 ? 0xffffffffu : ((1u << z) - 1u)) & ~((1u << a) - 1u);
-                    pairs += z - a;
-                    uint32_t hit = 0;
+                // all 64 columns of this thread in one round trip to TMEM
+                uint32_t raw[2][32];
+                tmem_ld32_issue(taddr, raw[0]);
+                tmem_ld32_issue(taddr + 32, raw[1]);
+                tmem_wait_ld();
+                const int cb0 = half * (kTcN / 2);
+                // columns of this thread inside [s0, s1)
+                const int ca = max(jlo - cb0, 0), cz = min(jhi - cb0, kTcN / 2);
+                if (q >= 0 && ca < cz) {
+                    pairs += cz - ca;
+                    // the filter value of every column, reduced to its minimum:
+                    // a column survives iff its value is <= thr, so a minimum
+                    // above thr (the common case) clears all 64 at once
+                    float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float2 xv = xs[cb + j];
-                        const float lhs = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x));
-                        hit |= (lhs <= thr ? 1u : 0u) << j;
+                    for (int j = 0; j < kTcN / 2; j += 4) {
+                        const float4 x01 = *reinterpret_cast<const float4 *>(xs + cb0 + j);
+                        const float4 x23 = *reinterpret_cast<const float4 *>(xs + cb0 + j + 2);
+                        m0 = fminf(m0, fmaf(-2.0f, __uint_as_float(raw[j >> 5][(j & 31) + 0]), fmaf(-qa, x01.y, x01.x)));
+                        m1 = fminf(m1, fmaf(-2.0f, __uint_as_float(raw[j >> 5][(j & 31) + 1]), fmaf(-qa, x01.w, x01.z)));
+                        m2 = fminf(m2, fmaf(-2.0f, __uint_as_float(raw[j >> 5][(j & 31) + 2]), fmaf(-qa, x23.y, x23.x)));
+                        m3 = fminf(m3, fmaf(-2.0f, __uint_as_float(raw[j >> 5][(j & 31) + 3]), fmaf(-qa, x23.w, x23.z)));
                     }
-                    hit &= valid;
-                    if (A.dbg_lo) {
-                        for (int j = a; j < z; ++j) {
-                            const float2 xv = xs[cb + j];
-                            const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
-                            const float bs = lo + 2.0f * qa * xv.y;
-                            A.dbg_lo[(int64_t)q * A.N + row0 + cb + j] = lo;
-                            A.dbg_up[(int64_t)q * A.N + row0 + cb + j] =
-                                bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
-                        }
-                    }
-                    while (hit) {
-                        // survivor: exact lower / upper bounds in the
-                        // certified form (rounded outward)
-                        const int j = __ffs(hit) - 1;
-                        hit &= hit - 1;
-                        const float2 xv = xs[cb + j];
-                        const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
-                        const float bs = lo + 2.0f * qa * xv.y;
-                        const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
-                        if (kl && up < kth) {
-                            int m = 0;
-                            for (int i = 1; i < kl; ++i) if (kb[i * 256] > kb[m * 256]) m = i;
-                            kb[m * 256] = up;
-                            float mx = kb[0];
-                            for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i * 256]);
-                            kth = mx;
-                        }
-                        if (lo <= U) {
-                            const int slot = atomicAdd(&A.cand_cnt[q], 1);
-                            if (slot < A.cand_C) {
-                                A.cand_p[(int64_t)q * A.cand_C + slot] = (int32_t)(row0 + cb + j);
-                                A.cand_lb[(int64_t)q * A.cand_C + slot] = lo;
-                                ++my_cand;
-                            } else {
-                                atomicOr(&A.qflag[q], 1);
+                    const bool any = fminf(fminf(m0, m1), fminf(m2, m3)) <= thr;
+                    if (any || A.dbg_lo) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int cb = cb0 + 32 * h;
+                            const int a = max(jlo - cb, 0), z = min(jhi - cb, 32);
+                            if (a >= z) continue;
+                            const uint32_t valid =
+                                (z >= 32 ? 0xffffffffu : ((1u << z) - 1u)) & ~((1u << a) - 1u);
+                            float v[32];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[h][j]);
+                            uint32_t hit = 0;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const float2 xv = xs[cb + j];
+                                const float lhs = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x));
+                                hit |= (lhs <= thr ? 1u : 0u) << j;
+                            }
+                            hit &= valid;
+                            if (A.dbg_lo) {
+                                for (int j = a; j < z; ++j) {
+                                    const float2 xv = xs[cb + j];
+                                    const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
+                                    const float bs = lo + 2.0f * qa * xv.y;
+                                    A.dbg_lo[(int64_t)q * A.N + row0 + cb + j] = lo;
+                                    A.dbg_up[(int64_t)q * A.N + row0 + cb + j] =
+                                        bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
+                                }
+                            }
+                            while (hit) {
+                                // survivor: exact lower / upper bounds in the
+                                // certified form (rounded outward)
+                                const int j = __ffs(hit) - 1;
+                                hit &= hit - 1;
+                                const float2 xv = xs[cb + j];
+                                const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
+                                const float bs = lo + 2.0f * qa * xv.y;
+                                const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
+                                if (kl && up < kth) {
+                                    int mi = 0;
+                                    for (int i = 1; i < kl; ++i) if (kb[i * 256] > kb[mi * 256]) mi = i;
+                                    kb[mi * 256] = up;
+                                    float mx = kb[0];
+                                    for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i * 256]);
+                                    kth = mx;
+                                }
+                                if (lo <= U) {
+                                    const int slot = atomicAdd(&A.cand_cnt[q], 1);
+                                    if (slot < A.cand_C) {
+                                        A.cand_p[(int64_t)q * A.cand_C + slot] = (int32_t)(row0 + cb + j);
+                                        A.cand_lb[(int64_t)q * A.cand_C + slot] = lo;
+                                        ++my_cand;
+                                    } else {
+                                        atomicOr(&A.qflag[q], 1);
+                                    }
+                                }
                             }
                         }
                     }
