@@ -416,6 +416,13 @@ def main():
                                   peak=pk["hbm_gbs"], unit="GB/s",
                                   note="16-bit rows + norms copied per query block (L2 serves repeats)"),
                     kernel_share_of_step=tc_s / t_dev)
+        tca_s = agg.get("tc_approx_ns", 0) / 1e9
+        if tca_s:
+            roof["approx_step_launches"] = dict(
+                kernel="k_tc_scan", share_of_step=tca_s / t_dev,
+                hbm_side=dict(achieved=agg["tc_approx_bytes"] / tca_s / 1e9, peak=pk["hbm_gbs"], unit="GB/s"),
+                note="the same kernel on each query's approximate-search leaves (few queries per "
+                     "leaf: bound by the 16-bit rows it streams, not by the MMA)")
         if plain:
             roof["plain_k_scan"] = plain_roof(plain)
 
@@ -450,7 +457,8 @@ def main():
                      series_candidate=agg["series_candidate"], sax_pruned=agg["series_sax_pruned"],
                      abandoned=agg["series_abandoned"], full=agg["series_full"],
                      points=agg["points_computed"], tc_pairs=agg["tc_pairs"],
-                     tc_candidates=agg["tc_candidates"], rescored=agg["rescored"],
+                     tc_candidates=agg["tc_candidates"], tc_approx_pairs=agg.get("tc_approx_pairs", 0),
+                     rescored=agg["rescored"],
                      retried=agg["retried_queries"], fallback=agg["fallback_queries"],
                      skip_sequential=agg["skip_sequential"]),
         index=dict(build_s=t_build, gen_s=t_gen, leaves=info["leaves"], depth=info["depth"],

@@ -140,6 +140,10 @@ typedef struct {
     int64_t tc_ns;                /* tensor-core kernel time (HK_Q_TIMING), ns   */
     int64_t tc_bytes;             /* 16-bit rows and norms the tensor-core kernel
                                      copied in (per query block)                 */
+    int64_t tc_approx_pairs;      /* the approximate step's distances on tensor
+                                     cores (k <= 16; tc_* count the exact step)  */
+    int64_t tc_approx_ns;         /* its kernel time (HK_Q_TIMING), ns           */
+    int64_t tc_approx_bytes;      /* its 16-bit rows and norms copied in         */
 } hk_query_stats;
 
 /*

@@ -268,6 +268,7 @@ uint32_t tc_idesc(int fmt);
 double tc_error_coefficient(int n, int fmt);
 float tc_eb2();
 constexpr int kTcMaxLen = 256;     // longest series the tensor-core form takes
+constexpr int kTcLocalK = 16;     // largest k whose best upper bounds the tensor-core scan tracks
 
 // Exhaustive exact k-NN into caller device buffers using only `sc`.
 void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,

@@ -55,8 +55,9 @@ enum StatIdx {
     ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_APPROX, ST_LEAVES_CAND, ST_SERIES_CAND,
     ST_SAX_PRUNED, ST_ABANDONED, ST_FULL, ST_POINTS, ST_RESCORED, ST_FALLBACK,
     ST_ITEMS, ST_SKIPSEQ, ST_SCAN_NS, ST_LAUNCHES, ST_SCAN_BYTES, ST_RETRIED, ST_TC_PAIRS,
-    ST_TC_CANDS, ST_TC_BYTES
+    ST_TC_CANDS, ST_TC_BYTES, ST_TCA_PAIRS, ST_TCA_CANDS, ST_TCA_BYTES, ST_COUNT
 };
+static_assert(ST_COUNT <= kStatSlots, "stat slots");
 
 struct ScanArgs {
     LeafView v;
@@ -861,6 +862,67 @@ void scan_phase(Workspace &ws, const LeafView &v, ScanArgs a, const ScanConfig &
     if (timer) timer->mark(s);
 }
 
+// a5-a7 on the tensor cores over the leaves whose mask value is `val`:
+// distances with a certified bound (k_tc_scan), then the exact float32
+// rescore of the survivors at or below U into the pool.  U only falls: the
+// scan lowers it from the k best upper bounds each thread has seen.
+void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, int nq, int k, int S_tc,
+              uint8_t val, int pool_C, float rho, int stat_pairs, int stat_cands, int stat_bytes,
+              cudaStream_t s, ScanTimer *tctimer) {
+    const int n = idx->n;
+    const int cand_C = std::max(65536, 256 * k);
+    ws.cand_cnt.reserve(nq, s);
+    ws.cand_p.reserve((size_t)nq * cand_C, s);
+    ws.cand_lb.reserve((size_t)nq * cand_C, s);
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.cand_cnt.p, 0, nq * sizeof(int32_t), s));
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p + 2, 0, sizeof(int32_t), s));
+    build_lists(ws, v, 128, S_tc, val, nq, s);
+    TcArgs t{};
+    t.Xb = idx->Xb.p;
+    t.xq = idx->xq.p;
+    t.n = n;
+    t.Qb = ws.Qb.p;
+    t.q2e = ws.q2.p;
+    t.qa = ws.qa.p;
+    t.qoff2 = ws.qoff.p;
+    t.eb2 = tc_eb2();
+    t.leaf_off = v.leaf_off;
+    t.L = v.L;
+    t.leaf_qoff = ws.leaf_qoff.p;
+    t.leaf_q = ws.leaf_q.p;
+    t.item_off = ws.item_off.p;
+    t.work_ctr = ws.counters.p;
+    t.S_T = S_tc;
+    t.U = ws.U.p;
+    t.k = k;
+    t.cand_cnt = ws.cand_cnt.p;
+    t.cand_p = ws.cand_p.p;
+    t.cand_lb = ws.cand_lb.p;
+    t.cand_C = cand_C;
+    t.qflag = ws.qflag.p;
+    t.err = ws.counters.p + 2;
+    t.stats = (long long *)ws.stats.p;
+    t.stat_pairs = stat_pairs;
+    t.stat_cands = stat_cands;
+    t.stat_bytes = stat_bytes;
+    t.idesc = tc_idesc(idx->fmt16);
+    t.dbg_lo = nullptr;
+    t.dbg_up = nullptr;
+    t.N = idx->N;
+    if (tctimer) tctimer->mark(s);
+    launch_tc_scan(t, s);
+    if (tctimer) tctimer->mark(s);
+    k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+    HK_CHECK_LAUNCH();
+    launch_tc_rescore(Qd, v.X, n, nq, ws.cand_cnt.p, ws.cand_p.p, ws.cand_lb.p, cand_C, ws.U.p,
+                      ws.pool_d.p, ws.pool_p.p, ws.pool_cnt.p, pool_C, ws.qflag.p,
+                      (long long *)ws.stats.p, ST_FULL, s);
+    int32_t terr = 0;
+    HK_CHECK_CUDA(cudaMemcpyAsync(&terr, ws.counters.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (terr) fail(HK_ETIMEOUT, "tensor-core scan: a bounded wait ran out (flag %d)", terr);
+}
+
 struct Prepared {
     int pool_C;
     ScanConfig cfg;
@@ -989,6 +1051,8 @@ void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s, Scan
     stats->tc_pairs = st[ST_TC_PAIRS];
     stats->tc_candidates = st[ST_TC_CANDS];
     stats->tc_bytes = st[ST_TC_BYTES];
+    stats->tc_approx_pairs = st[ST_TCA_PAIRS];
+    stats->tc_approx_bytes = st[ST_TCA_BYTES];
     stats->scan_ns = timer ? timer->total_ns() : 0;
     stats->kernel_launches = launches;
 }
@@ -1024,7 +1088,7 @@ namespace {
 // U_init: initial bounds (device, float bits) or nullptr for +inf; with
 // bounds given, the approximate search is skipped.
 void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, const hk_query_opts &o,
-                cudaStream_t s, const uint32_t *U_init, ScanTimer *timer, ScanTimer *tctimer,
+                cudaStream_t s, const uint32_t *U_init, ScanTimer *timer, ScanTimer *tctimer, ScanTimer *tcatimer,
                 std::vector<int32_t> &flags, std::vector<uint32_t> &Uh) {
     const int n = idx->n;
     const int64_t L = idx->L;
@@ -1078,6 +1142,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         HK_CHECK_CUDA(cudaStreamSynchronize(s));
         if (bad) fail(HK_EINVAL, "queries have values beyond the 16-bit copy's range");
     }
+    const int S_tc = o.series_tile > 0 ? o.series_tile : 65536;
     // a1 + a2
     k_qprep<<<nq, 256, n * sizeof(float), s>>>(Qd, n, idx->seg_ab.p, idx->S, idx->bp.p, ws.qseg.p,
                                                nosax ? nullptr : reinterpret_cast<__half *>(ws.sax_tab.p));
@@ -1122,10 +1187,18 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         k_approx_select<<<nq, 256, 0, s>>>(ws.lb.p, L, idx->leaf_off.p, l_max, k, nq, kAmax, ws.approx.p,
                                            ws.qcand.p, ws.mask.p);
         HK_CHECK_LAUNCH();
-        ScanArgs aa = a;
-        aa.use_sax = 0;
-        aa.lb = nullptr;
-        scan_phase(ws, v, aa, cfg, 1, nq, s, timer);
+        if (tc && k <= kTcLocalK) {
+            // on the tensor cores from U = +inf: each thread's k best upper
+            // bounds lower U after its first tile, so only the first tile of
+            // a row keeps every column for the exact rescore
+            tc_phase(idx, ws, v, Qd, nq, k, S_tc, 1, pool_C, rho, ST_TCA_PAIRS, ST_TCA_CANDS, ST_TCA_BYTES,
+                     s, tcatimer);
+        } else {
+            ScanArgs aa = a;
+            aa.use_sax = 0;
+            aa.lb = nullptr;
+            scan_phase(ws, v, aa, cfg, 1, nq, s, timer);
+        }
         k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
                                                    (long long *)ws.stats.p, -1, ST_LEAVES_APPROX);
         HK_CHECK_LAUNCH();
@@ -1149,58 +1222,8 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     if (tc) {
         // a9: tensor-core distances with a certified bound, then the exact
         // float32 rescore of the survivors into the pool
-        const int cand_C = std::max(65536, 256 * k);
-        ws.cand_cnt.reserve(nq, s);
-        ws.cand_p.reserve((size_t)nq * cand_C, s);
-        ws.cand_lb.reserve((size_t)nq * cand_C, s);
-        HK_CHECK_CUDA(cudaMemsetAsync(ws.cand_cnt.p, 0, nq * sizeof(int32_t), s));
-        HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p + 2, 0, sizeof(int32_t), s));
-        const int S_tc = o.series_tile > 0 ? o.series_tile : 16384;
-        build_lists(ws, v, 128, S_tc, 2, nq, s);
-        TcArgs t{};
-        t.Xb = idx->Xb.p;
-        t.xq = idx->xq.p;
-        t.n = n;
-        t.Qb = ws.Qb.p;
-        t.q2e = ws.q2.p;
-        t.qa = ws.qa.p;
-        t.qoff2 = ws.qoff.p;
-        t.eb2 = tc_eb2();
-        t.leaf_off = v.leaf_off;
-        t.L = L;
-        t.leaf_qoff = ws.leaf_qoff.p;
-        t.leaf_q = ws.leaf_q.p;
-        t.item_off = ws.item_off.p;
-        t.work_ctr = ws.counters.p;
-        t.S_T = S_tc;
-        t.U = ws.U.p;
-        t.k = k;
-        t.cand_cnt = ws.cand_cnt.p;
-        t.cand_p = ws.cand_p.p;
-        t.cand_lb = ws.cand_lb.p;
-        t.cand_C = cand_C;
-        t.qflag = ws.qflag.p;
-        t.err = ws.counters.p + 2;
-        t.stats = (long long *)ws.stats.p;
-        t.stat_pairs = ST_TC_PAIRS;
-        t.stat_cands = ST_TC_CANDS;
-        t.stat_bytes = ST_TC_BYTES;
-        t.idesc = tc_idesc(idx->fmt16);
-        t.dbg_lo = nullptr;
-        t.dbg_up = nullptr;
-        t.N = idx->N;
-        if (tctimer) tctimer->mark(s);
-        launch_tc_scan(t, s);
-        if (tctimer) tctimer->mark(s);
-        k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
-        HK_CHECK_LAUNCH();
-        launch_tc_rescore(Qd, v.X, n, nq, ws.cand_cnt.p, ws.cand_p.p, ws.cand_lb.p, cand_C, ws.U.p,
-                          ws.pool_d.p, ws.pool_p.p, ws.pool_cnt.p, pool_C, ws.qflag.p,
-                          (long long *)ws.stats.p, ST_FULL, s);
-        int32_t terr = 0;
-        HK_CHECK_CUDA(cudaMemcpyAsync(&terr, ws.counters.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        HK_CHECK_CUDA(cudaStreamSynchronize(s));
-        if (terr) fail(HK_ETIMEOUT, "tensor-core scan: a bounded wait ran out (flag %d)", terr);
+        tc_phase(idx, ws, v, Qd, nq, k, S_tc, 2, pool_C, rho, ST_TC_PAIRS, ST_TC_CANDS, ST_TC_BYTES, s,
+                 tctimer);
     } else {
         scan_phase(ws, v, a, cfg, 2, nq, s, timer);
     }
@@ -1222,11 +1245,11 @@ void run_query_ws(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float
                   const hk_query_opts &o, cudaStream_t s, int64_t *out_ids, float *out_dist,
                   hk_query_stats *stats) {
     const long long launches0 = g_launches;
-    ScanTimer timer, tctimer;
-    timer.on = tctimer.on = (o.flags & HK_Q_TIMING) != 0;
+    ScanTimer timer, tctimer, tcatimer;
+    timer.on = tctimer.on = tcatimer.on = (o.flags & HK_Q_TIMING) != 0;
     std::vector<int32_t> flags;
     std::vector<uint32_t> Uh;
-    query_pass(idx, ws, Qd, nq, k, o, s, nullptr, &timer, &tctimer, flags, Uh);
+    query_pass(idx, ws, Qd, nq, k, o, s, nullptr, &timer, &tctimer, &tcatimer, flags, Uh);
 
     // Queries whose lists or pool overflowed: run them again starting from
     // their final bound, which is tight, so far fewer candidates qualify.
@@ -1248,7 +1271,7 @@ void run_query_ws(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float
         // near-ties that crowd the precision form's wider band fit its lists
         hk_query_opts o2 = o;
         o2.flags &= ~HK_Q_BF16;
-        query_pass(idx, w2, w2.Q.p, nsub, k, o2, s, w2.Uinit.p, &timer, &tctimer, flags2, U2);
+        query_pass(idx, w2, w2.Q.p, nsub, k, o2, s, w2.Uinit.p, &timer, &tctimer, &tcatimer, flags2, U2);
         LeafView v;
         v.X = idx->X.p;
         v.perm = idx->perm.p;
@@ -1280,7 +1303,10 @@ void run_query_ws(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float
     copy_out(ws, nq, k, out_ids, out_dist, s);
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
     copy_stats(ws, stats, s, &timer, g_launches - launches0);
-    if (stats) stats->tc_ns = tctimer.total_ns();
+    if (stats) {
+        stats->tc_ns = tctimer.total_ns();
+        stats->tc_approx_ns = tcatimer.total_ns();
+    }
 }
 
 void run_scan(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k, cudaStream_t s,

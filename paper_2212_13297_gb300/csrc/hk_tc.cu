@@ -26,16 +26,19 @@
 // single bulk copy (cp.async.bulk) places in shared memory in exactly the
 // layout the MMA descriptor describes: leading-dimension offset 128 bytes
 // (next 8 points), stride-dimension offset (n/8)*128 bytes (next 8 series).
-// The query block is gathered into the same layout with ordinary stores.
+// The query block lives in tensor memory (row i in lane i, two 16-bit
+// points per 32-bit column), so each MMA reads only the series tile from
+// shared memory.
 //
-// CTA roles (10 warps): warp 0 issues the bulk copies (series tiles by
-// K-chunks, and the tile's norm pairs), warp 1 (one thread) issues tcgen05.mma and
-// tcgen05.commit, warps 2-9 read the accumulators with tcgen05.ld and filter:
-// warp w reads TMEM lane quarter w%4 (query rows 32(w%4)..+31) and half of
-// the tile's columns.  Per element the filter is two FMAs and a compare
-// against a per-row threshold; the exact bounds are formed only for the
-// rare survivors.
-// Sixteen shared-memory chunk stages for series tiles, two TMEM accumulators.  Every
+// CTA roles (18 warps): warp 0 issues the bulk copies (a whole series tile
+// and its norm pairs per stage), warp 1 (one thread) issues tcgen05.mma and
+// tcgen05.commit, warps 2-17 write the query block into tensor memory at the
+// start of each item, then read the accumulators with tcgen05.ld and
+// filter: warp w reads TMEM lane quarter w%4 (query rows 32(w%4)..+31) and a
+// quarter of the tile's columns.  Per element the filter is two FMAs and a
+// minimum; the per-column test and the exact bounds are formed only when a
+// minimum reaches the row's threshold.
+// Two shared-memory stages for series tiles, three TMEM accumulators.  Every
 // mbarrier wait is bounded; on a timeout the CTA raises an error flag,
 // drains, frees its tensor memory and stops.
 #include <cuda_bf16.h>
@@ -55,16 +58,22 @@ constexpr int kTcN = 128;        // series per tile (MMA N)
 // bulk copy each.
 constexpr int kTcStages = 2;
 constexpr int kTcStageBytes = kTcN * 256 * 2;   // longest series (256 points)
-// Norm slots: tile g uses slot g % 8.  The producer is at most kTcStages
-// tiles ahead of the MMA, which is at most 2 ahead of the epilogue: when the
-// producer writes tile g's norms, tile g-8 (the slot's previous user) was
-// read long before.
+// Norm slots: tile g uses slot g % 8.  The producer writes tile g's norms
+// after the MMA finished tile g - kTcStages, which it issued after the
+// epilogue released tile g - kTcStages - kAcc: tile g-8 (the slot's previous
+// user) was read before.
 constexpr int kNormSlots = 8;
 constexpr int kTcEpiWarps = 8;   // two per TMEM lane quarter, each half the columns
+constexpr int kTcEpiThreads = 32 * kTcEpiWarps;
+constexpr int kEpiChunks = kTcN / 32 / (kTcEpiWarps / 4);   // 32-column chunks per epilogue warp
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
-constexpr int kTmemCols = 256;   // two accumulators of kTcN columns
+constexpr int kAcc = 3;          // accumulators in tensor memory
+constexpr int kTmemCols = 512;   // kAcc accumulators of kTcN columns, then the query block
+constexpr int kTmemA = kAcc * kTcN; // first column of the query block (n/2 <= 128 columns)
+static_assert(kTmemA + 128 <= kTmemCols, "tensor memory overflow");
+static_assert(kNormSlots >= kTcStages + kAcc + 1, "norm slot reuse distance");
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far above any legitimate wait
-constexpr int kLocalK = 32;
+constexpr int kLocalK = kTcLocalK;   // k-best upper bounds kept per epilogue thread
 constexpr double kTcEb = 0x1p-19;   // relative term for norm and epilogue rounding
 constexpr float kF16Max = 65504.0f;      // 2k up to this tightens U per row
 
@@ -136,9 +145,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
@@ -154,13 +160,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
     return d;                 // base offset 0, swizzle none
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (tensor memory) += A (tensor memory) * B (shared memory descriptor)^T
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -182,6 +189,21 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32
           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]),
+        "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]),
+        "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -189,8 +211,8 @@ __device__ __forceinline__ void tmem_wait_ld() {
 struct TcShared {
     uint64_t full[kTcStages];
     uint64_t empty[kTcStages];
-    uint64_t acc_full[2];
-    uint64_t acc_empty[2];
+    uint64_t acc_full[kAcc];
+    uint64_t acc_empty[kAcc];
     uint32_t tmem_base;
     int abort_flag;
     int64_t item;
@@ -205,14 +227,12 @@ struct TcShared {
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     const int n = A.n;
-    const uint32_t a_bytes = (uint32_t)kTcM * n * 2;
     const uint32_t b_bytes = (uint32_t)kTcN * n * 2;             // a whole tile
     const int nst = kTcStages;
-    unsigned char *sA = tc_smem;                             // 1024-aligned
-    unsigned char *sB = tc_smem + a_bytes;                   // stages follow
+    unsigned char *sB = tc_smem;                             // 1024-aligned stages
     float2 *sX = reinterpret_cast<float2 *>(sB + kTcStages * kTcStageBytes);  // kNormSlots * kTcN
-    float *kbest = reinterpret_cast<float *>(sX + kNormSlots * kTcN);      // kTcM * kLocalK
-    TcShared &S = *reinterpret_cast<TcShared *>(kbest + kTcM * kLocalK);
+    float *kbest = reinterpret_cast<float *>(sX + kNormSlots * kTcN);      // kTcEpiThreads * kLocalK
+    TcShared &S = *reinterpret_cast<TcShared *>(kbest + kTcEpiThreads * kLocalK);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -220,7 +240,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kAcc; ++b) {
             mbar_init(&S.acc_full[b], 1);
             mbar_init(&S.acc_empty[b], 32 * kTcEpiWarps);
         }
@@ -239,7 +259,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     tc_fence_after();
     const uint32_t tmem = S.tmem_base;
     const int64_t total = A.item_off[A.L];
-    const uint32_t lbo = 128, sbo = (uint32_t)(n / 8) * 128;   // A: full K resident
+    const uint32_t lbo = 128, sbo = (uint32_t)(n / 8) * 128;   // series tile, K-major core matrices
 
     // running counts of barrier completions (phases), kept per role
     uint32_t g_tile = 0;   // tiles processed by this CTA so far (all roles agree)
@@ -268,22 +288,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
             for (int g = 0; g < kTcM; ++g) S.qid[g] = g < S.gq ? lq[g] : -1;
         }
         __syncthreads();
-        // gather the query block into the core-matrix layout (zeros past gq);
-        // consecutive threads fill consecutive 16-byte rows of a core matrix
-        {
-            const int kc = n / 8;
-            const int chunks = kTcM * kc;   // 16-byte pieces
-            for (int c = tid; c < chunks; c += kTcThreads) {
-                const int rr = c & 7, k8 = (c >> 3) % kc, r8 = (c >> 3) / kc;
-                const int r = r8 * 8 + rr;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                const int q = S.qid[r];
-                if (q >= 0) v = *reinterpret_cast<const uint4 *>(A.Qb + (int64_t)q * n + k8 * 8);
-                *reinterpret_cast<uint4 *>(sA + (r8 * kc + k8) * 128 + rr * 16) = v;
+        // the query block into tensor memory: epilogue warp w writes lane
+        // quarter w%4, 32-column chunks c (points 64c..64c+63) of its column
+        // group (w-2)/4; zeros past gq and past n
+        if (warp >= 2) {
+            const int r = (warp & 3) * 32 + lane;
+            const int q = S.qid[r];
+#pragma unroll 1
+            for (int h = 0; h < kEpiChunks; ++h) {
+                const int c = ((warp - 2) >> 2) * kEpiChunks + h;
+                if (64 * c >= n) break;
+                uint32_t w[32];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    const int k0 = 64 * c + 8 * i;
+                    if (q >= 0 && k0 < n) v = *reinterpret_cast<const uint4 *>(A.Qb + (int64_t)q * n + k0);
+                    w[4 * i + 0] = v.x;
+                    w[4 * i + 1] = v.y;
+                    w[4 * i + 2] = v.z;
+                    w[4 * i + 3] = v.w;
+                }
+                tmem_st32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(kTmemA + 32 * c), w);
             }
-            fence_proxy_async();
+            tmem_wait_st();
         }
+        tc_fence_before();
         __syncthreads();
+        tc_fence_after();
         const int T = S.tiles;
         const int64_t base = S.base, s0 = S.s0, s1 = S.s1;
         if (tid == 0) my_bytes += (long long)T * (b_bytes + kTcN * (long long)sizeof(float2));
@@ -306,32 +338,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
         } else if (warp == 1) {
             // ---------------- MMA issuer
             if (lane == 0) {
-                const uint32_t a_base = smem_u32(sA);
+                const uint32_t a_tmem = tmem + (uint32_t)kTmemA;
                 const int ksteps = n / 16;
                 for (int t = 0; t < T; ++t) {
                     const uint32_t gt = g_tile + t;
                     const int s = gt % nst;
                     const uint32_t use = gt / nst;
-                    const int b = gt & 1;
-                    const uint32_t ause = gt >> 1;
+                    const int b = gt % kAcc;
+                    const uint32_t ause = gt / kAcc;
                     if (ause > 0 && !mbar_wait(&S.acc_empty[b], (ause - 1) & 1, &S.abort_flag)) break;
                     if (!mbar_wait(&S.full[s], use & 1, &S.abort_flag)) break;
                     tc_fence_after();
                     const uint32_t b_base = smem_u32(sB + s * kTcStageBytes);
                     const uint32_t d = tmem + (uint32_t)(b * kTcN);
                     for (int ks = 0; ks < ksteps; ++ks) {
-                        const uint64_t ad = smem_desc(a_base + ks * 2 * 128, lbo, sbo);
+                        // K step: 16 points = 8 columns of A, 2 core matrices of B
                         const uint64_t bd = smem_desc(b_base + ks * 2 * 128, lbo, sbo);
-                        mma_bf16(d, ad, bd, A.idesc, ks > 0 ? 1u : 0u);
+                        mma_ts(d, a_tmem + (uint32_t)(ks * 8), bd, A.idesc, ks > 0 ? 1u : 0u);
                     }
                     mma_commit(&S.empty[s]);
                     mma_commit(&S.acc_full[b]);
                 }
             }
         } else {
-            // ---------------- epilogue: thread owns query row r, half the columns
+            // ---------------- epilogue: thread owns query row r, a quarter of the columns
             const int r = (warp & 3) * 32 + lane;   // TMEM lane quarter of this warp
-            const int half = (warp - 2) >> 2;       // column half
+            const int cq = (warp - 2) >> 2;         // column group
             const int q = S.qid[r];
             float q2e = 0.f, qa = 0.f, qoff2 = 0.f, U = 0.f;
             if (q >= 0) {
@@ -341,18 +373,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                 U = __uint_as_float(A.U[q]);
             }
             // the k best upper bounds of this thread: slot i of epilogue thread
-            // e at kbest[i * 256 + e] (conflict-free); the two column halves
-            // of a row keep separate lists
+            // e at kbest[i * kTcEpiThreads + e] (conflict-free); the column
+            // quarters of a row keep separate lists
             float *kb = kbest + (tid - 64);
-            const int kl = (A.k <= kLocalK / 2) ? A.k : 0;
-            for (int i = 0; i < kl; ++i) kb[i * 256] = INFINITY;
+            const int kl = (A.k <= kLocalK) ? A.k : 0;
+            for (int i = 0; i < kl; ++i) kb[i * kTcEpiThreads] = INFINITY;
             float kth = INFINITY;      // k-th smallest upper bound seen by this thread
             long long pairs = 0;
             for (int t = 0; t < T; ++t) {
                 const uint32_t gt = g_tile + t;
-                const int b = gt & 1;
-                const int s = gt % kTcStages;
-                const uint32_t ause = gt >> 1;
+                const int b = gt % kAcc;
+                const uint32_t ause = gt / kAcc;
                 if (!mbar_wait_warp(&S.acc_full[b], ause & 1, &S.abort_flag)) break;
                 tc_fence_after();
                 if (q >= 0 && (t & 7) == 0) U = fminf(U, __uint_as_float(A.U[q]));
@@ -362,91 +393,89 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                 const int jhi = (int)min((int64_t)kTcN, s1 - row0);
                 const float thr = U - q2e;   // lo <= U  <=>  x2e - qa|x| - 2v <= U - q2e
                 const float2 *xs = sX + (gt % kNormSlots) * kTcN;
-                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                                       (uint32_t)(b * kTcN + half * (kTcN / 2));
-                // all 64 columns of this thread in one round trip to TMEM
-                uint32_t raw[2][32];
-                tmem_ld32_issue(taddr, raw[0]);
-                tmem_ld32_issue(taddr + 32, raw[1]);
+                uint32_t raw[kEpiChunks][32];
+#pragma unroll
+                for (int h = 0; h < kEpiChunks; ++h)
+                    tmem_ld32_issue(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                        (uint32_t)(b * kTcN + (cq * kEpiChunks + h) * 32),
+                                    raw[h]);
                 tmem_wait_ld();
-                const int cb0 = half * (kTcN / 2);
+#pragma unroll
+                for (int h = 0; h < kEpiChunks; ++h) {
+                const int cb = (cq * kEpiChunks + h) * 32;
                 // columns of this thread inside [s0, s1)
-                const int ca = max(jlo - cb0, 0), cz = min(jhi - cb0, kTcN / 2);
-                if (q >= 0 && ca < cz) {
-                    pairs += cz - ca;
+                const int a = max(jlo - cb, 0), z = min(jhi - cb, 32);
+                if (q >= 0 && a < z) {
+                    pairs += z - a;
                     // the filter value of every column, reduced to its minimum:
                     // a column survives iff its value is <= thr, so a minimum
-                    // above thr (the common case) clears all 64 at once
+                    // above thr (the common case) clears all 32 at once
                     float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
 #pragma unroll
-                    for (int j = 0; j < kTcN / 2; j += 4) {
-                        const float4 x01 = *reinterpret_cast<const float4 *>(xs + cb0 + j);
-                        const float4 x23 = *reinterpret_cast<const float4 *>(xs + cb0 + j + 2);
-                        m0 = fminf(m0, fmaf(-2.0f, __uint_as_float(raw[j >> 5][(j & 31) + 0]), fmaf(-qa, x01.y, x01.x)));
-                        m1 = fminf(m1, fmaf(-2.0f, __uint_as_float(raw[j >> 5][(j & 31) + 1]), fmaf(-qa, x01.w, x01.z)));
-                        m2 = fminf(m2, fmaf(-2.0f, __uint_as_float(raw[j >> 5][(j & 31) + 2]), fmaf(-qa, x23.y, x23.x)));
-                        m3 = fminf(m3, fmaf(-2.0f, __uint_as_float(raw[j >> 5][(j & 31) + 3]), fmaf(-qa, x23.w, x23.z)));
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 x01 = *reinterpret_cast<const float4 *>(xs + cb + j);
+                        const float4 x23 = *reinterpret_cast<const float4 *>(xs + cb + j + 2);
+                        m0 = fminf(m0, fmaf(-2.0f, __uint_as_float(raw[h][j + 0]), fmaf(-qa, x01.y, x01.x)));
+                        m1 = fminf(m1, fmaf(-2.0f, __uint_as_float(raw[h][j + 1]), fmaf(-qa, x01.w, x01.z)));
+                        m2 = fminf(m2, fmaf(-2.0f, __uint_as_float(raw[h][j + 2]), fmaf(-qa, x23.y, x23.x)));
+                        m3 = fminf(m3, fmaf(-2.0f, __uint_as_float(raw[h][j + 3]), fmaf(-qa, x23.w, x23.z)));
                     }
                     const bool any = fminf(fminf(m0, m1), fminf(m2, m3)) <= thr;
                     if (any || A.dbg_lo) {
+                        const uint32_t valid =
+                            (z >= 32 ? 0xffffffffu : ((1u << z) - 1u)) & ~((1u << a) - 1u);
+                        float v[32];
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int cb = cb0 + 32 * h;
-                            const int a = max(jlo - cb, 0), z = min(jhi - cb, 32);
-                            if (a >= z) continue;
-                            const uint32_t valid =
-                                (z >= 32 ? 0xffffffffu : ((1u << z) - 1u)) & ~((1u << a) - 1u);
-                            float v[32];
+                        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[h][j]);
+                        uint32_t hit = 0;
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[h][j]);
-                            uint32_t hit = 0;
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const float2 xv = xs[cb + j];
-                                const float lhs = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x));
-                                hit |= (lhs <= thr ? 1u : 0u) << j;
-                            }
-                            hit &= valid;
-                            if (A.dbg_lo) {
-                                for (int j = a; j < z; ++j) {
-                                    const float2 xv = xs[cb + j];
-                                    const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
-                                    const float bs = lo + 2.0f * qa * xv.y;
-                                    A.dbg_lo[(int64_t)q * A.N + row0 + cb + j] = lo;
-                                    A.dbg_up[(int64_t)q * A.N + row0 + cb + j] =
-                                        bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
-                                }
-                            }
-                            while (hit) {
-                                // survivor: exact lower / upper bounds in the
-                                // certified form (rounded outward)
-                                const int j = __ffs(hit) - 1;
-                                hit &= hit - 1;
+                        for (int j = 0; j < 32; ++j) {
+                            const float2 xv = xs[cb + j];
+                            const float lhs = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x));
+                            hit |= (lhs <= thr ? 1u : 0u) << j;
+                        }
+                        hit &= valid;
+                        if (A.dbg_lo) {
+                            for (int j = a; j < z; ++j) {
                                 const float2 xv = xs[cb + j];
                                 const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
                                 const float bs = lo + 2.0f * qa * xv.y;
-                                const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
-                                if (kl && up < kth) {
-                                    int mi = 0;
-                                    for (int i = 1; i < kl; ++i) if (kb[i * 256] > kb[mi * 256]) mi = i;
-                                    kb[mi * 256] = up;
-                                    float mx = kb[0];
-                                    for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i * 256]);
-                                    kth = mx;
-                                }
-                                if (lo <= U) {
-                                    const int slot = atomicAdd(&A.cand_cnt[q], 1);
-                                    if (slot < A.cand_C) {
-                                        A.cand_p[(int64_t)q * A.cand_C + slot] = (int32_t)(row0 + cb + j);
-                                        A.cand_lb[(int64_t)q * A.cand_C + slot] = lo;
-                                        ++my_cand;
-                                    } else {
-                                        atomicOr(&A.qflag[q], 1);
-                                    }
+                                A.dbg_lo[(int64_t)q * A.N + row0 + cb + j] = lo;
+                                A.dbg_up[(int64_t)q * A.N + row0 + cb + j] =
+                                    bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
+                            }
+                        }
+                        while (hit) {
+                            // survivor: exact lower / upper bounds in the
+                            // certified form (rounded outward)
+                            const int j = __ffs(hit) - 1;
+                            hit &= hit - 1;
+                            const float2 xv = xs[cb + j];
+                            const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
+                            const float bs = lo + 2.0f * qa * xv.y;
+                            const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
+                            if (kl && up < kth) {
+                                int mi = 0;
+                                for (int i = 1; i < kl; ++i)
+                                    if (kb[i * kTcEpiThreads] > kb[mi * kTcEpiThreads]) mi = i;
+                                kb[mi * kTcEpiThreads] = up;
+                                float mx = kb[0];
+                                for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i * kTcEpiThreads]);
+                                kth = mx;
+                            }
+                            if (lo <= U) {
+                                const int slot = atomicAdd(&A.cand_cnt[q], 1);
+                                if (slot < A.cand_C) {
+                                    A.cand_p[(int64_t)q * A.cand_C + slot] = (int32_t)(row0 + cb + j);
+                                    A.cand_lb[(int64_t)q * A.cand_C + slot] = lo;
+                                    ++my_cand;
+                                } else {
+                                    atomicOr(&A.qflag[q], 1);
                                 }
                             }
                         }
                     }
+                }
                 }
                 tc_fence_before();
                 mbar_arrive(&S.acc_empty[b]);
@@ -602,8 +631,9 @@ __global__ void k_tc_rescore(const float *__restrict__ Q, const float *__restric
 }
 
 size_t tc_smem_bytes(int n) {
-    return (size_t)kTcM * n * 2 + (size_t)kTcStages * kTcStageBytes + (size_t)kNormSlots * kTcN * 8 +
-           (size_t)kTcM * kLocalK * 4 + sizeof(TcShared) + 1024;
+    (void)n;   // stages are sized for the longest series
+    return (size_t)kTcStages * kTcStageBytes + (size_t)kNormSlots * kTcN * 8 +
+           (size_t)kTcEpiThreads * kLocalK * 4 + sizeof(TcShared) + 1024;
 }
 
 uint32_t tc_idesc(int fmt) {
