@@ -33,9 +33,11 @@ WORKLOADS = {
                   desc="100M random walks x 256, leaf 100K, 10K hard queries (sigma 0.5/1.0), k=10"),
     "mid": dict(N=10_000_000, n=256, tau=10_000, nq=100, sigmas=[0.01, 0.1, 0.5, 1.0], k=10, batch=100,
                 desc="10M random walks x 256, leaf 10K, 100 queries (sigma 0.01/0.1/0.5/1.0), k=10"),
-    # 2 GB cases of the large workload's shape, for profiler captures
+    # 2-6 GB cases of the large workload's shape, for profiler captures
     "tcprofile": dict(N=2_000_000, n=256, tau=20_000, nq=1000, sigmas=[0.5, 1.0], k=10, batch=1000,
                       desc="2M random walks x 256, leaf 20K, 1000 hard queries (sigma 0.5/1.0), k=10"),
+    "tcleaf100k": dict(N=4_000_000, n=256, tau=100_000, nq=1000, sigmas=[0.5, 1.0], k=10, batch=1000,
+                       desc="4M random walks x 256, leaf 100K, 1000 hard queries (sigma 0.5/1.0), k=10"),
     "profile": dict(N=2_000_000, n=256, tau=10_000, nq=200, sigmas=[0.5, 1.0], k=10, batch=200,
                     desc="2M random walks x 256, leaf 10K, 200 hard queries (sigma 0.5/1.0), k=10"),
     "small": dict(N=100_000, n=256, tau=1_000, nq=10, sigmas=[0.1], k=1, batch=10,

@@ -38,7 +38,7 @@
 // quarter of the tile's columns.  Per element the filter is two FMAs and a
 // minimum; the per-column test and the exact bounds are formed only when a
 // minimum reaches the row's threshold.
-// Two shared-memory stages for series tiles, three TMEM accumulators.  Every
+// Three shared-memory stages for series tiles, three TMEM accumulators.  Every
 // mbarrier wait is bounded; on a timeout the CTA raises an error flag,
 // drains, frees its tensor memory and stops.
 #include <cuda_bf16.h>
@@ -56,7 +56,7 @@ constexpr int kTcN = 128;        // series per tile (MMA N)
 // Series tiles (128 series, 16 groups of 8: one contiguous run in the
 // core-matrix layout) stream through kTcStages shared-memory stages, one
 // bulk copy each.
-constexpr int kTcStages = 2;
+constexpr int kTcStages = 3;
 constexpr int kTcStageBytes = kTcN * 256 * 2;   // longest series (256 points)
 // Norm slots: tile g uses slot g % 8.  The producer writes tile g's norms
 // after the MMA finished tile g - kTcStages, which it issued after the
@@ -208,6 +208,15 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// One work item: series [s0, s1) of a leaf against a block of up to 128 of
+// the leaf's queries; tiles of 128 series start at base (8-aligned).
+struct TcItem {
+    int64_t it;            // item number; >= the item count: no more work
+    int64_t s0, s1, base;
+    int tiles, gq;
+    int qid[kTcM];         // query ids of the block's rows, -1 past gq
+};
+
 struct TcShared {
     uint64_t full[kTcStages];
     uint64_t empty[kTcStages];
@@ -215,11 +224,57 @@ struct TcShared {
     uint64_t acc_empty[kAcc];
     uint32_t tmem_base;
     int abort_flag;
-    int64_t item;
-    int64_t s0, s1, base;
-    int tiles, gq, leaf;
-    int qid[kTcM];
+    TcItem item;
 };
+
+// Claim the next work item and describe it in D (one warp).  The leaf is
+// the last l with item_off[l] <= it, found by a 32-way search (three rounds
+// of one coalesced probe each for ~2,000 leaves).
+__device__ void fetch_item(const TcArgs &A, int64_t total, TcItem &D, int lane) {
+    int64_t it = 0;
+    if (lane == 0) it = atomicAdd(A.work_ctr, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (lane == 0) D.it = it;
+    if (it >= total) {
+        __syncwarp();
+        return;
+    }
+    int lo = 0, hi = (int)A.L;   // item_off[lo] <= it < item_off[hi + 1]
+    while (hi - lo > 31) {
+        const int64_t span = hi - lo;
+        const int pos = lo + (int)(span * (lane + 1) / 32);
+        const unsigned m = __ballot_sync(0xffffffffu, A.item_off[pos] <= it);
+        const int last = m ? 31 - __clz((int)m) : -1;
+        const int nlo = last >= 0 ? lo + (int)(span * (last + 1) / 32) : lo;
+        const int nhi = last < 31 ? lo + (int)(span * (last + 2) / 32) - 1 : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    {
+        const int pos = lo + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, pos <= hi && A.item_off[pos] <= it);
+        lo += 31 - __clz((int)m);
+    }
+    const int leaf = lo;
+    const int64_t local = it - A.item_off[leaf];
+    const int qoff = A.leaf_qoff[leaf];
+    const int nql = A.leaf_qoff[leaf + 1] - qoff;
+    const int ngroups = (nql + kTcM - 1) / kTcM;
+    const int64_t tile = local / ngroups;
+    const int grp = (int)(local % ngroups);
+    const int gq = min(kTcM, nql - grp * kTcM);
+    if (lane == 0) {
+        const int64_t lo_s = A.leaf_off[leaf], hi_s = A.leaf_off[leaf + 1];
+        D.s0 = lo_s + tile * A.S_T;
+        D.s1 = min(D.s0 + (int64_t)A.S_T, hi_s);
+        D.base = D.s0 & ~(int64_t)7;
+        D.tiles = (int)((D.s1 - D.base + kTcN - 1) / kTcN);
+        D.gq = gq;
+    }
+    const int32_t *lq = A.leaf_q + qoff + grp * kTcM;
+    for (int g = lane; g < kTcM; g += 32) D.qid[g] = g < gq ? lq[g] : -1;
+    __syncwarp();
+}
 
 }  // namespace
 
@@ -265,35 +320,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     uint32_t g_tile = 0;   // tiles processed by this CTA so far (all roles agree)
     long long my_cand = 0, my_pairs = 0, my_bytes = 0;
 
+    // Items are claimed when a CTA is ready for one, so the query blocks of
+    // a leaf range start together and share its tiles in L2.
     for (;;) {
-        if (tid == 0) S.item = atomicAdd(A.work_ctr, 1);
+        if (warp == 0) fetch_item(A, total, S.item, lane);
         __syncthreads();
-        const int64_t it = S.item;
-        if (it >= total || S.abort_flag) break;
-        if (tid == 0) {
-            const int leaf = find_segment<int64_t>(A.item_off, (int)A.L + 1, it);
-            const int64_t local = it - A.item_off[leaf];
-            const int nql = A.leaf_qoff[leaf + 1] - A.leaf_qoff[leaf];
-            const int ngroups = (nql + kTcM - 1) / kTcM;
-            const int64_t tile = local / ngroups;
-            const int grp = (int)(local % ngroups);
-            const int64_t lo = A.leaf_off[leaf], hi = A.leaf_off[leaf + 1];
-            S.s0 = lo + tile * A.S_T;
-            S.s1 = min(S.s0 + (int64_t)A.S_T, hi);
-            S.base = S.s0 & ~(int64_t)7;
-            S.tiles = (int)((S.s1 - S.base + kTcN - 1) / kTcN);
-            S.gq = min(kTcM, nql - grp * kTcM);
-            S.leaf = leaf;
-            const int32_t *lq = A.leaf_q + A.leaf_qoff[leaf] + grp * kTcM;
-            for (int g = 0; g < kTcM; ++g) S.qid[g] = g < S.gq ? lq[g] : -1;
-        }
-        __syncthreads();
+        const TcItem &D = S.item;
+        if (D.it >= total || S.abort_flag) break;
         // the query block into tensor memory: epilogue warp w writes lane
         // quarter w%4, 32-column chunks c (points 64c..64c+63) of its column
         // group (w-2)/4; zeros past gq and past n
         if (warp >= 2) {
             const int r = (warp & 3) * 32 + lane;
-            const int q = S.qid[r];
+            const int q = D.qid[r];
 #pragma unroll 1
             for (int h = 0; h < kEpiChunks; ++h) {
                 const int c = ((warp - 2) >> 2) * kEpiChunks + h;
@@ -316,8 +355,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        const int T = S.tiles;
-        const int64_t base = S.base, s0 = S.s0, s1 = S.s1;
+        const int T = D.tiles;
+        const int64_t base = D.base, s0 = D.s0, s1 = D.s1;
         if (tid == 0) my_bytes += (long long)T * (b_bytes + kTcN * (long long)sizeof(float2));
 
         if (warp == 0) {
@@ -364,7 +403,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
             // ---------------- epilogue: thread owns query row r, a quarter of the columns
             const int r = (warp & 3) * 32 + lane;   // TMEM lane quarter of this warp
             const int cq = (warp - 2) >> 2;         // column group
-            const int q = S.qid[r];
+            const int q = D.qid[r];
             float q2e = 0.f, qa = 0.f, qoff2 = 0.f, U = 0.f;
             if (q >= 0) {
                 q2e = A.q2e[q];
