@@ -104,6 +104,13 @@ int hk_index_info_get(const hk_index *idx, hk_index_info *out);
                               leaves on the tensor cores from the index's
                               16-bit copy (HK_BUILD_BF16 or HK_BUILD_FP16,
                               n <= 256), certified error bound, exact rescore */
+#define HK_Q_GRAPH 32u     /* replay the query pass from a CUDA graph: the
+                              first call with a given (nq, k, options) runs
+                              normally and records the pass; later calls with
+                              the same key copy Q into the index's graph work
+                              space and replay it (same answers).  The index
+                              holds one graph; calls on one index must not run
+                              concurrently.  HK_Q_TIMING is ignored.          */
 
 typedef struct {
     int32_t l_max;        /* leaves visited by the approximate search per query
@@ -246,6 +253,33 @@ int hk_poll(hk_server *sv, uint64_t ticket, int64_t *ids, float *dist,
             int32_t timeout_us, int64_t *latency_ns);
 int hk_server_stats_get(hk_server *sv, hk_server_stats *out);
 int hk_server_destroy(hk_server *sv);
+
+/* ---- tuning ------------------------------------------------------------------ */
+
+typedef struct {
+    hk_query_opts opts;     /* the fastest configuration found               */
+    double ms_per_query;    /* its wall time per query on the sample          */
+    int32_t tried;          /* configurations timed                           */
+    int32_t tensor_cores;   /* 1: the fastest uses the precision form          */
+} hk_tune_result;
+
+/*
+ * hk_tune -- choose the query path's configuration for a workload by timing
+ * the candidates on a sample batch Q[nq][n] (host or device) with k
+ * neighbours.  The paper tunes its parameters by hand (Sec. 4.2,
+ * Parameterization); every candidate gives the same exact answer, so only
+ * time decides.  Candidates: the float32 form with query_group in {2, 4, 8},
+ * series_tile in {4096, 8192, 16384} and EAPCA_TH in {0.25, 1.01 (every
+ * query skip-sequential)}; and, when the index has a 16-bit copy and
+ * n <= 256, the precision form (HK_Q_BF16) with series_tile in {16384,
+ * 32768, 65536, 131072}.  Each candidate runs once untimed, then twice
+ * timed (the faster counts); a candidate whose untimed run already takes
+ * over twice the best time so far is dropped.  keep_flags (HK_Q_NOSAX,
+ * HK_Q_NOTHRESH) are kept in every candidate; l_max and sax_th take their
+ * defaults.  The result's opts can be passed to hk_query as they are.
+ */
+int hk_tune(hk_index *idx, const float *Q, int32_t nq, int32_t k, uint32_t keep_flags, void *stream,
+            hk_tune_result *out);
 
 /*
  * hk_isax_breakpoints -- the 255 iSAX breakpoints the library uses

@@ -31,6 +31,7 @@ HK_Q_NOTHRESH = 2
 HK_Q_NOPRUNE = 4
 HK_Q_TIMING = 8
 HK_Q_BF16 = 16
+HK_Q_GRAPH = 32
 
 
 class hk_build_opts(ctypes.Structure):
@@ -64,6 +65,11 @@ class hk_index_info(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class hk_tune_result(ctypes.Structure):
+    _fields_ = [("opts", hk_query_opts), ("ms_per_query", ctypes.c_double), ("tried", ctypes.c_int32),
+                ("tensor_cores", ctypes.c_int32)]
+
+
 class hk_server_opts(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64), ("query_flags", ctypes.c_uint32),
@@ -88,7 +94,7 @@ EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_scan_knn"
            "hk_scan_knn_noalloc",
            "hk_isax_breakpoints", "hk_index_export", "hk_debug_lb_eapca", "hk_debug_lb_sax",
            "hk_debug_tc_dist", "hk_server_create", "hk_server_add", "hk_submit", "hk_poll",
-           "hk_server_stats_get", "hk_server_destroy",
+           "hk_server_stats_get", "hk_server_destroy", "hk_tune",
            "hk_last_error", "hk_version"]
 
 
@@ -126,6 +132,8 @@ def lib():
                               ctypes.POINTER(ctypes.c_int64)]
         L.hk_server_stats_get.argtypes = [vp, ctypes.POINTER(hk_server_stats)]
         L.hk_server_destroy.argtypes = [vp]
+        L.hk_tune.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, vp,
+                              ctypes.POINTER(hk_tune_result)]
         L.hk_last_error.restype = ctypes.c_char_p
         L.hk_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -223,6 +231,18 @@ class Index:
         _check(lib().hk_query(self._h, _ptr(Q), nq, int(k), ctypes.byref(o), _stream(stream),
                               _ptr(ids), _ptr(dist), ctypes.byref(st)))
         return ids, dist, st.as_dict()
+
+    def tune(self, Q, k: int, keep_flags=0, stream=None):
+        """hk_tune: the fastest query configuration on the sample batch Q, as a
+        dict of hk_query keyword arguments plus ms_per_query / tried /
+        tensor_cores."""
+        r = hk_tune_result()
+        _check(lib().hk_tune(self._h, _ptr(Q), Q.shape[0], int(k), int(keep_flags), _stream(stream),
+                             ctypes.byref(r)))
+        o = r.opts
+        return dict(l_max=o.l_max, eapca_th=o.eapca_th, sax_th=o.sax_th, flags=o.flags,
+                    query_group=o.query_group, series_tile=o.series_tile,
+                    ms_per_query=r.ms_per_query, tried=r.tried, tensor_cores=r.tensor_cores)
 
     def export(self):
         """Leaf layout as numpy arrays (see hk_index_export)."""

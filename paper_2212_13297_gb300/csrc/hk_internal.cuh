@@ -126,6 +126,25 @@ struct Workspace {
     DevBuf<float> cand_lb;      // nq * cand_C  lower bound D~ - E
     DevBuf<uint32_t> Uinit;     // retry pass: starting bounds
     DevBuf<int32_t> sel;        // retry pass: rows of the batch it answers
+    // graph mode: the captured pass (reading Q, writing out_*) and its key
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey[4] = {0, 0, 0, 0};
+    long long glaunches = 0;    // kernels in the graph
+    cudaStream_t gstream = nullptr;   // the stream graph-mode work runs on (capturable)
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    Workspace() = default;
+    Workspace(const Workspace &) = delete;
+    Workspace &operator=(const Workspace &) = delete;
+    ~Workspace() {
+        drop_graph();
+        if (gstream) cudaStreamDestroy(gstream);
+        for (cudaEvent_t e : gev)
+            if (e) cudaEventDestroy(e);
+    }
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+    }
 };
 
 // Device view of a collection laid out by leaves (an index, or a plain
@@ -176,6 +195,7 @@ struct hk_index {
 
     hk::Workspace ws;
     hk::Workspace ws_retry;
+    hk::Workspace ws_graph;    // HK_Q_GRAPH calls only: its buffers stay where the graph points
 };
 
 namespace hk {

@@ -575,6 +575,13 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
 }
 
 // U = min(U, (1+rho) x k-th smallest pooled float32 distance).
+__global__ void k_stats_init(long long *__restrict__ stats, int nq, long long L) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        stats[ST_QUERIES] = nq;
+        stats[ST_LEAVES_TOTAL] = (long long)nq * L;
+    }
+}
+
 __global__ void k_pool_kth(const float *__restrict__ pool_d, const int32_t *__restrict__ pool_cnt,
                            int C, int k, float rho, uint32_t *__restrict__ U) {
     __shared__ int red[32];
@@ -868,14 +875,13 @@ void scan_phase(Workspace &ws, const LeafView &v, ScanArgs a, const ScanConfig &
 // scan lowers it from the k best upper bounds each thread has seen.
 void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, int nq, int k, int S_tc,
               uint8_t val, int pool_C, float rho, int stat_pairs, int stat_cands, int stat_bytes,
-              cudaStream_t s, ScanTimer *tctimer) {
+              cudaStream_t s, ScanTimer *tctimer, bool capture) {
     const int n = idx->n;
     const int cand_C = std::max(65536, 256 * k);
     ws.cand_cnt.reserve(nq, s);
     ws.cand_p.reserve((size_t)nq * cand_C, s);
     ws.cand_lb.reserve((size_t)nq * cand_C, s);
     HK_CHECK_CUDA(cudaMemsetAsync(ws.cand_cnt.p, 0, nq * sizeof(int32_t), s));
-    HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p + 2, 0, sizeof(int32_t), s));
     build_lists(ws, v, 128, S_tc, val, nq, s);
     TcArgs t{};
     t.Xb = idx->Xb.p;
@@ -917,6 +923,7 @@ void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, 
     launch_tc_rescore(Qd, v.X, n, nq, ws.cand_cnt.p, ws.cand_p.p, ws.cand_lb.p, cand_C, ws.U.p,
                       ws.pool_d.p, ws.pool_p.p, ws.pool_cnt.p, pool_C, ws.qflag.p,
                       (long long *)ws.stats.p, ST_FULL, s);
+    if (capture) return;
     int32_t terr = 0;
     HK_CHECK_CUDA(cudaMemcpyAsync(&terr, ws.counters.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -959,7 +966,8 @@ void copy_out(const Workspace &ws, int nq, int k, int64_t *ids, float *dist, cud
 // a8: tighten U from the pool, rescore in binary64 and select.  Returns the
 // per-query flags (bit0: a list or the pool overflowed) and bounds on the host.
 void final_select(Workspace &ws, const LeafView &v, const float *Qd, int nq, int k, int pool_C,
-                  float rho, cudaStream_t s, std::vector<int32_t> &flags, std::vector<uint32_t> &U) {
+                  float rho, cudaStream_t s, std::vector<int32_t> &flags, std::vector<uint32_t> &U,
+                  bool capture = false) {
     k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
     HK_CHECK_LAUNCH();
     HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p + 1, 0, sizeof(int32_t), s));
@@ -967,6 +975,7 @@ void final_select(Workspace &ws, const LeafView &v, const float *Qd, int nq, int
                                ws.U.p, ws.qflag.p, k, rho, ws.rs_d.p, ws.out_ids.p, ws.out_dist.p,
                                (long long *)ws.stats.p, ws.counters.p + 1, nullptr);
     HK_CHECK_LAUNCH();
+    if (capture) return;
     flags.assign(nq, 0);
     U.assign(nq, 0);
     int32_t err = 0;
@@ -1087,9 +1096,11 @@ namespace {
 // One pass of the query path over a batch (a1-a8 without the retries).
 // U_init: initial bounds (device, float bits) or nullptr for +inf; with
 // bounds given, the approximate search is skipped.
+// capture: only enqueue work (the pass is being recorded into a graph); the
+// flags, bounds and error words stay on the device for the caller to read.
 void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, const hk_query_opts &o,
                 cudaStream_t s, const uint32_t *U_init, ScanTimer *timer, ScanTimer *tctimer, ScanTimer *tcatimer,
-                std::vector<int32_t> &flags, std::vector<uint32_t> &Uh) {
+                std::vector<int32_t> &flags, std::vector<uint32_t> &Uh, bool capture = false) {
     const int n = idx->n;
     const int64_t L = idx->L;
     const float rho = rho_for(n);
@@ -1121,12 +1132,9 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         k_fill_u32<<<64, 256, 0, s>>>(ws.U.p, nq, 0x7f800000u);
         HK_CHECK_LAUNCH();
     }
-    {
-        long long init[kStatSlots] = {0};
-        init[ST_QUERIES] = nq;
-        init[ST_LEAVES_TOTAL] = (long long)nq * L;
-        HK_CHECK_CUDA(cudaMemcpyAsync(ws.stats.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
-    }
+    k_stats_init<<<1, 32, 0, s>>>((long long *)ws.stats.p, nq, L);
+    HK_CHECK_LAUNCH();
+    HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p, 0, 4 * sizeof(int32_t), s));
 
     if (tc) {
         ws.Qb.reserve((size_t)nq * n, s);
@@ -1137,10 +1145,12 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         HK_CHECK_CUDA(cudaMemsetAsync(ws.bad.p, 0, sizeof(int), s));
         launch_tc_qprep(Qd, nq, n, idx->fmt16, idx->xn_max, ws.Qb.p, ws.q2.p, ws.qa.p, ws.qoff.p,
                         ws.bad.p, s);
-        int bad = 0;
-        HK_CHECK_CUDA(cudaMemcpyAsync(&bad, ws.bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        HK_CHECK_CUDA(cudaStreamSynchronize(s));
-        if (bad) fail(HK_EINVAL, "queries have values beyond the 16-bit copy's range");
+        if (!capture) {
+            int bad = 0;
+            HK_CHECK_CUDA(cudaMemcpyAsync(&bad, ws.bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            HK_CHECK_CUDA(cudaStreamSynchronize(s));
+            if (bad) fail(HK_EINVAL, "queries have values beyond the 16-bit copy's range");
+        }
     }
     const int S_tc = o.series_tile > 0 ? o.series_tile : 65536;
     // a1 + a2
@@ -1192,7 +1202,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
             // bounds lower U after its first tile, so only the first tile of
             // a row keeps every column for the exact rescore
             tc_phase(idx, ws, v, Qd, nq, k, S_tc, 1, pool_C, rho, ST_TCA_PAIRS, ST_TCA_CANDS, ST_TCA_BYTES,
-                     s, tcatimer);
+                     s, tcatimer, capture);
         } else {
             ScanArgs aa = a;
             aa.use_sax = 0;
@@ -1223,7 +1233,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         // a9: tensor-core distances with a certified bound, then the exact
         // float32 rescore of the survivors into the pool
         tc_phase(idx, ws, v, Qd, nq, k, S_tc, 2, pool_C, rho, ST_TC_PAIRS, ST_TC_CANDS, ST_TC_BYTES, s,
-                 tctimer);
+                 tctimer, capture);
     } else {
         scan_phase(ws, v, a, cfg, 2, nq, s, timer);
     }
@@ -1231,7 +1241,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
                                                (long long *)ws.stats.p, ST_SERIES_CAND, -1);
     HK_CHECK_LAUNCH();
     // a8: boundary rescore and answer
-    final_select(ws, v, Qd, nq, k, pool_C, rho, s, flags, Uh);
+    final_select(ws, v, Qd, nq, k, pool_C, rho, s, flags, Uh, capture);
 }
 
 }  // namespace
@@ -1241,16 +1251,139 @@ void run_query(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opt
     run_query_ws(idx, idx->ws, idx->ws_retry, Qd, nq, k, o, s, out_ids, out_dist, stats);
 }
 
+namespace {
+
+// The rest of a query after its pass: retries of the queries whose lists or
+// pool overflowed, the answers out, the counters.
+void finish_query(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float *Qd, int nq, int k,
+                  const hk_query_opts &o, cudaStream_t s, int64_t *out_ids, float *out_dist,
+                  hk_query_stats *stats, const std::vector<int32_t> &flags, long long launches0,
+                  ScanTimer &timer, ScanTimer &tctimer, ScanTimer &tcatimer);
+
+// Graph mode: the pass for this (batch size, k, options) is captured once
+// into a CUDA graph over the graph work space and replayed; the queries are
+// copied into the work space's input buffer first.  The first call with a
+// new key answers with an ordinary pass (which sizes every buffer), then
+// records the same pass for the calls after it.
+void run_query_graph_on(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opts &o, cudaStream_t s,
+                        int64_t *out_ids, float *out_dist, hk_query_stats *stats);
+
+void run_query_graph(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opts &o, cudaStream_t s,
+                     int64_t *out_ids, float *out_dist, hk_query_stats *stats) {
+    // the work runs on the work space's own stream (the caller's may be the
+    // legacy default stream, which cannot be captured), ordered after the
+    // caller's stream and before what the caller enqueues next
+    Workspace &ws = idx->ws_graph;
+    if (!ws.gstream) {
+        HK_CHECK_CUDA(cudaStreamCreateWithFlags(&ws.gstream, cudaStreamNonBlocking));
+        HK_CHECK_CUDA(cudaEventCreateWithFlags(&ws.gev[0], cudaEventDisableTiming));
+        HK_CHECK_CUDA(cudaEventCreateWithFlags(&ws.gev[1], cudaEventDisableTiming));
+    }
+    HK_CHECK_CUDA(cudaEventRecord(ws.gev[0], s));
+    HK_CHECK_CUDA(cudaStreamWaitEvent(ws.gstream, ws.gev[0], 0));
+    try {
+        run_query_graph_on(idx, Qd, nq, k, o, ws.gstream, out_ids, out_dist, stats);
+    } catch (...) {
+        cudaEventRecord(ws.gev[1], ws.gstream);
+        cudaStreamWaitEvent(s, ws.gev[1], 0);
+        throw;
+    }
+    HK_CHECK_CUDA(cudaEventRecord(ws.gev[1], ws.gstream));
+    HK_CHECK_CUDA(cudaStreamWaitEvent(s, ws.gev[1], 0));
+}
+
+void run_query_graph_on(hk_index *idx, const float *Qd, int nq, int k, const hk_query_opts &o, cudaStream_t s,
+                        int64_t *out_ids, float *out_dist, hk_query_stats *stats) {
+    Workspace &ws = idx->ws_graph;
+    const long long launches0 = g_launches;
+    ScanTimer timer, tctimer, tcatimer;   // off: a replay is not timed per kernel
+    const int n = idx->n;
+    hk_query_opts oq = o;
+    oq.flags &= ~(uint32_t)(HK_Q_GRAPH | HK_Q_TIMING);
+    uint64_t key[4];
+    key[0] = ((uint64_t)(uint32_t)nq << 32) | (uint32_t)k;
+    key[1] = ((uint64_t)oq.flags << 32) | (uint32_t)oq.l_max;
+    key[2] = ((uint64_t)(uint32_t)oq.query_group << 32) | (uint32_t)oq.series_tile;
+    uint32_t th[2];
+    std::memcpy(&th[0], &oq.eapca_th, 4);
+    std::memcpy(&th[1], &oq.sax_th, 4);
+    key[3] = ((uint64_t)th[0] << 32) | th[1];
+    const float *in_before = ws.Q.p;
+    ws.Q.reserve((size_t)nq * n, s);
+    const bool fresh = ws.gexec == nullptr || ws.Q.p != in_before ||
+                       std::memcmp(key, ws.gkey, sizeof(key)) != 0;
+    HK_CHECK_CUDA(cudaMemcpyAsync(ws.Q.p, Qd, (size_t)nq * n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    std::vector<int32_t> flags;
+    std::vector<uint32_t> Uh;
+    if (fresh) {
+        ws.drop_graph();
+        query_pass(idx, ws, ws.Q.p, nq, k, oq, s, nullptr, nullptr, nullptr, nullptr, flags, Uh);
+        const long long l0 = g_launches;
+        cudaGraph_t g = nullptr;
+        HK_CHECK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            std::vector<int32_t> f2;
+            std::vector<uint32_t> u2;
+            query_pass(idx, ws, ws.Q.p, nq, k, oq, s, nullptr, nullptr, nullptr, nullptr, f2, u2, true);
+        } catch (...) {
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        HK_CHECK_CUDA(cudaStreamEndCapture(s, &g));
+        const cudaError_t e = cudaGraphInstantiate(&ws.gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ws.gexec = nullptr;
+            fail(HK_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
+        }
+        ws.glaunches = g_launches - l0;
+        g_launches = l0;   // recorded, not run
+        std::memcpy(ws.gkey, key, sizeof(key));
+    } else {
+        HK_CHECK_CUDA(cudaGraphLaunch(ws.gexec, s));
+        g_launches += ws.glaunches;
+        flags.assign(nq, 0);
+        int32_t ctr[4] = {0, 0, 0, 0};
+        int bad = 0;
+        HK_CHECK_CUDA(cudaMemcpyAsync(flags.data(), ws.qflag.p, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaMemcpyAsync(ctr, ws.counters.p, sizeof(ctr), cudaMemcpyDeviceToHost, s));
+        if (oq.flags & HK_Q_BF16)
+            HK_CHECK_CUDA(cudaMemcpyAsync(&bad, ws.bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (bad) fail(HK_EINVAL, "queries have values beyond the 16-bit copy's range");
+        if (ctr[2]) fail(HK_ETIMEOUT, "tensor-core scan: a bounded wait ran out (flag %d)", ctr[2]);
+        if (ctr[1]) fail(HK_EINTERNAL, "a query had fewer than k candidates after the scan");
+    }
+    finish_query(idx, ws, idx->ws_retry, ws.Q.p, nq, k, oq, s, out_ids, out_dist, stats, flags, launches0,
+                 timer, tctimer, tcatimer);
+}
+
+}  // namespace
+
 void run_query_ws(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float *Qd, int nq, int k,
                   const hk_query_opts &o, cudaStream_t s, int64_t *out_ids, float *out_dist,
                   hk_query_stats *stats) {
+    if (o.flags & HK_Q_GRAPH) {
+        run_query_graph(idx, Qd, nq, k, o, s, out_ids, out_dist, stats);
+        return;
+    }
     const long long launches0 = g_launches;
     ScanTimer timer, tctimer, tcatimer;
     timer.on = tctimer.on = tcatimer.on = (o.flags & HK_Q_TIMING) != 0;
     std::vector<int32_t> flags;
     std::vector<uint32_t> Uh;
     query_pass(idx, ws, Qd, nq, k, o, s, nullptr, &timer, &tctimer, &tcatimer, flags, Uh);
+    finish_query(idx, ws, ws_retry, Qd, nq, k, o, s, out_ids, out_dist, stats, flags, launches0, timer, tctimer,
+                 tcatimer);
+}
 
+namespace {
+
+void finish_query(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float *Qd, int nq, int k,
+                  const hk_query_opts &o, cudaStream_t s, int64_t *out_ids, float *out_dist,
+                  hk_query_stats *stats, const std::vector<int32_t> &flags, long long launches0,
+                  ScanTimer &timer, ScanTimer &tctimer, ScanTimer &tcatimer) {
     // Queries whose lists or pool overflowed: run them again starting from
     // their final bound, which is tight, so far fewer candidates qualify.
     std::vector<int32_t> sel;
@@ -1308,6 +1441,8 @@ void run_query_ws(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float
         stats->tc_approx_ns = tcatimer.total_ns();
     }
 }
+
+}  // namespace
 
 void run_scan(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k, cudaStream_t s,
               int64_t *out_ids, float *out_dist) {

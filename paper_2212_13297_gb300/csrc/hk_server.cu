@@ -170,7 +170,7 @@ void worker_loop(hk_server *sv, Worker *w) {
             std::memset(&o, 0, sizeof(o));
             o.eapca_th = -1.0f;
             o.sax_th = -1.0f;
-            o.flags = sv->opts.query_flags & ~(uint32_t)HK_Q_TIMING;
+            o.flags = sv->opts.query_flags & ~(uint32_t)(HK_Q_TIMING | HK_Q_GRAPH);
             if ((o.flags & HK_Q_BF16) && !idx->has_bf16) o.flags &= ~(uint32_t)HK_Q_BF16;
             hk::run_query_ws(idx, w->ws, w->ws_retry, w->Qd.p, nq, k, o, w->stream, w->ids_h,
                              w->dist_h, nullptr);

@@ -75,8 +75,11 @@ def test_binding_structs_match_header(hk):
         body = text[:text.index("} %s;" % struct_name)]
         body = body[body.rindex("typedef struct {"):]
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-        return re.findall(r"\b(?:u?int\d+_t|float|double)\s+(\w+)(?:\[\d+\])?;", body)
+        return re.findall(r"\b(?:u?int\d+_t|float|double|hk_\w+)\s+(\w+)(?:\[\d+\])?;", body)
 
     for cname, pyc in [("hk_build_opts", hk.hk_build_opts), ("hk_query_opts", hk.hk_query_opts),
-                       ("hk_query_stats", hk.hk_query_stats), ("hk_index_info", hk.hk_index_info)]:
+                       ("hk_query_stats", hk.hk_query_stats), ("hk_index_info", hk.hk_index_info),
+                       ("hk_tune_result", hk.hk_tune_result), ("hk_server_opts", hk.hk_server_opts),
+                       ("hk_server_stats", hk.hk_server_stats)]:
         assert [f[0] for f in pyc._fields_] == fields(cname), cname
+        assert ctypes.sizeof(pyc) >= 4 * len(pyc._fields_), cname
