@@ -44,6 +44,13 @@ WORKLOADS = {
                   desc="100K random walks x 256, leaf 1K, 10 queries (sigma 0.1), k=1"),
 }
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
+# capture committed under profiles/ (named beside each entry); a workload or
+# form without one reports traffic null.  Re-take them when the kernel changes.
+DRAM_TRAFFIC = {
+    ("large", "fp16"): dict(exact=69.32e9, approx=16.60e9, source="profiles/k_tc_scan_dram_100M_x256_fp16.md"),
+}
+
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
@@ -409,8 +416,11 @@ def main():
         flops = 2.0 * n * agg["tc_pairs"]
         ach = flops / tc_s / 1e12 if tc_s else None
         peak_t = pk.get("bf16_tflops_sustained") or 1713.1
+        dram = DRAM_TRAFFIC.get((args.workload, args.form))
         roof = dict(bound="tensor", achieved=ach, peak=peak_t, unit="TFLOP/s", frac=(ach or 0) / peak_t,
-                    traffic=None, kernel="k_tc_scan",
+                    traffic=dram["exact"] if dram else None, kernel="k_tc_scan",
+                    traffic_note=("DRAM bytes per exact-step launch (%s); algorithmic: the candidate "
+                                  "leaves' 16-bit rows once, about 25 GB" % dram["source"]) if dram else None,
                     peak_note="of measured sustained bf16 (%s); %s dense rate equals bf16's nominally; "
                               "2n flops per (query, series) pair" % (pk["source"], args.form),
                     frac_of_burst=(ach or 0) / (pk.get("bf16_tflops") or 1920.7),
@@ -423,6 +433,7 @@ def main():
             roof["approx_step_launches"] = dict(
                 kernel="k_tc_scan", share_of_step=tca_s / t_dev,
                 hbm_side=dict(achieved=agg["tc_approx_bytes"] / tca_s / 1e9, peak=pk["hbm_gbs"], unit="GB/s"),
+                traffic=dram["approx"] if dram else None,
                 note="the same kernel on each query's approximate-search leaves (few queries per "
                      "leaf: bound by the 16-bit rows it streams, not by the MMA)")
         if plain:
