@@ -95,7 +95,7 @@ void exclusive_scan_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t
 struct Workspace {
     DevBuf<float> Q;            // nq * n
     DevBuf<double> qseg;        // nq * S * 2  (mu, sd) per distinct segment
-    DevBuf<uint16_t> sax_tab;   // nq * 16 * 256 LB_SAX table (float16, rounded down)
+    DevBuf<float> sax_paa;      // nq * 32: PAA rounded down (16), then up (16)
     DevBuf<double> lb;          // nq * L
     DevBuf<uint32_t> U;         // nq   bound on the k-th distance (float bits)
     DevBuf<uint8_t> qmode;      // nq   bit0: LB_SAX filter on

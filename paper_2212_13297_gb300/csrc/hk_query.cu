@@ -63,7 +63,8 @@ struct ScanArgs {
     LeafView v;
     const float *Q;
     int nq;
-    const __half *sax_tab;     // nq*16*256 or nullptr
+    const float *sax_paa;      // nq*32: PAA rounded down (16), then up (16); nullptr: no LB_SAX
+    const float *bp;           // the 255 iSAX breakpoints
     const uint8_t *qmode;      // nq (bit0: LB_SAX on) or nullptr
     const double *lb;          // nq*L or nullptr
     uint32_t *U;               // nq float bits
@@ -93,14 +94,10 @@ __device__ __forceinline__ float upper_f(float d, float rho) { return __fmul_ru(
 // the LB_SAX table T[i][s] = (n/16) dist(PAA_i, cell s)^2 rounded down to
 // float16 (8 KB per query, so a scan CTA holds the tables of its queries).
 __global__ void k_qprep(const float *__restrict__ Q, int n, const int32_t *__restrict__ seg_ab,
-                        int64_t S, const float *__restrict__ bp, double *__restrict__ qseg,
-                        __half *__restrict__ tab) {
+                        int64_t S, double *__restrict__ qseg, float *__restrict__ paa_out) {
     extern __shared__ float qs[];
-    __shared__ double paa[kWord];
-    __shared__ float bps[255];
     const int q = blockIdx.x;
     for (int j = threadIdx.x; j < n; j += blockDim.x) qs[j] = Q[(int64_t)q * n + j];
-    for (int j = threadIdx.x; j < 255; j += blockDim.x) bps[j] = bp[j];
     __syncthreads();
     if (qseg) {
         for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
@@ -110,21 +107,40 @@ __global__ void k_qprep(const float *__restrict__ Q, int n, const int32_t *__res
             qseg[((int64_t)q * S + s) * 2 + 1] = sd;
         }
     }
-    if (tab) {
+    if (paa_out && threadIdx.x < kWord) {
+        // PAA (binary64) bracketed by float32 values below and above it
         const int l = n / kWord;
-        if (threadIdx.x < kWord)
-            paa[threadIdx.x] = seg_mean64(qs, threadIdx.x * l, (threadIdx.x + 1) * l);
-        __syncthreads();
-        const double w = (double)l;
-        for (int t = threadIdx.x; t < kWord * kAlpha; t += blockDim.x) {
-            const int i = t / kAlpha, sym = t % kAlpha;
-            const double lo = sym == 0 ? -INFINITY : (double)bps[sym - 1];
-            const double hi = sym == kAlpha - 1 ? INFINITY : (double)bps[sym];
-            const double d = dist_to_range64(paa[i], lo, hi);
-            // rounded down twice (binary64 -> float32 -> float16): a lower value
-            tab[(int64_t)q * kWord * kAlpha + t] =
-                __float2half_rd(__double2float_rd(__dmul_rn(w, __dmul_rn(d, d))));
-        }
+        const double m = seg_mean64(qs, threadIdx.x * l, (threadIdx.x + 1) * l);
+        paa_out[(int64_t)q * 2 * kWord + threadIdx.x] = __double2float_rd(m);
+        paa_out[(int64_t)q * 2 * kWord + kWord + threadIdx.x] = __double2float_ru(m);
+    }
+}
+
+// a5: LB_SAX of one iSAX word against one query, rounded down at every
+// step, so it never exceeds the exact value (binary64 PAA against the
+// float32 cells).  B[257]: -inf, the 255 breakpoints, +inf (cell of symbol s
+// is [B[s], B[s+1])); lo, hi: the word's cells; paa_lo / paa_hi: the query's
+// PAA rounded down / up; w = n/16.
+__device__ __forceinline__ float lb_sax_lower(const float (&lo)[kWord], const float (&hi)[kWord],
+                                             const float *paa_lo, const float *paa_hi, float w) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kWord; ++i) {
+        const float a = __fsub_rd(lo[i], paa_hi[i]);   // <= cell's low end - PAA
+        const float b = __fsub_rd(paa_lo[i], hi[i]);   // <= PAA - cell's high end
+        const float d = fmaxf(fmaxf(a, b), 0.0f);
+        acc = __fmaf_rd(d, d, acc);
+    }
+    return __fmul_rd(acc, w);
+}
+
+__device__ __forceinline__ void sax_cells(uint4 w4, const float *B, float (&lo)[kWord], float (&hi)[kWord]) {
+    const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+    for (int i = 0; i < kWord; ++i) {
+        const int sym = (wv[i >> 2] >> ((i & 3) * 8)) & 0xff;
+        lo[i] = B[sym];
+        hi[i] = B[sym + 1];
     }
 }
 
@@ -306,8 +322,7 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.v.n;
     float *q_s = reinterpret_cast<float *>(smem_raw);                 // G*n
-    __half *tab_s = reinterpret_cast<__half *>(q_s + G * n);          // G*4096 if use_sax
-    float *stage_d = reinterpret_cast<float *>(tab_s + (A.use_sax ? G * kWord * kAlpha : 0));
+    float *stage_d = q_s + G * n;
     int32_t *stage_p = reinterpret_cast<int32_t *>(stage_d + G * kBT);
     float *list_d = reinterpret_cast<float *>(stage_p + G * kBT);     // G*p2
     int32_t *list_p = reinterpret_cast<int32_t *>(list_d + G * A.p2);
@@ -320,11 +335,18 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
     __shared__ int64_t s_s0, s_s1;
     __shared__ int s_gq, s_leaf;
     __shared__ long long s_cnt[4];   // sax pruned, abandoned, full, points
+    __shared__ float s_B[kAlpha + 1];          // cell ends: -inf, breakpoints, +inf
+    __shared__ float s_paa[G][2 * kWord];      // per query: PAA rounded down, then up
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t total = A.item_off[A.v.L];
     const float rho = A.rho;
     long long my_sax = 0, my_ab = 0, my_full = 0, my_pts = 0, my_bytes = 0;
+    if (A.sax_paa) {
+        for (int j = tid; j <= kAlpha; j += kBT)
+            s_B[j] = j == 0 ? -INFINITY : (j == kAlpha ? INFINITY : A.bp[j - 1]);
+    }
+    const float w_sax = (float)(n / kWord);
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(A.work_ctr, 1);
@@ -380,11 +402,8 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
             const float4 *src = reinterpret_cast<const float4 *>(A.Q + (int64_t)s_qid[g] * n);
             float4 *dst = reinterpret_cast<float4 *>(q_s + g * n);
             for (int j = tid; j < (n >> 2); j += kBT) dst[j] = src[j];
-            if (sax_mask >> g & 1) {
-                const uint4 *ts = reinterpret_cast<const uint4 *>(A.sax_tab + (int64_t)s_qid[g] * kWord * kAlpha);
-                uint4 *td = reinterpret_cast<uint4 *>(tab_s + g * kWord * kAlpha);
-                for (int j = tid; j < kWord * kAlpha / 8; j += kBT) td[j] = ts[j];
-            }
+            if ((sax_mask >> g & 1) && tid < 2 * kWord)
+                s_paa[g][tid] = A.sax_paa[(int64_t)s_qid[g] * 2 * kWord + tid];
         }
         __syncthreads();
 
@@ -398,15 +417,12 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
                 for (int g = 0; g < G; ++g) T[g] = s_T[g];
                 if (sax_mask) {
                     const uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(A.v.sax) + s);
-                    const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                    float clo[kWord], chi[kWord];
+                    sax_cells(w4, s_B, clo, chi);
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         if (!(sax_mask >> g & 1)) continue;
-                        const __half *tg = tab_s + g * kWord * kAlpha;
-                        float lbs = 0.0f;
-#pragma unroll
-                        for (int i = 0; i < kWord; ++i)
-                            lbs += __half2float(tg[i * kAlpha + ((wv[i >> 2] >> ((i & 3) * 8)) & 0xff)]);
+                        const float lbs = lb_sax_lower(clo, chi, s_paa[g], s_paa[g] + kWord, w_sax);
                         if (lbs > s_Tsax[g]) {
                             act &= ~(1u << g);
                             ++my_sax;
@@ -737,14 +753,21 @@ __global__ void k_fill_u32(uint32_t *p, int64_t n, uint32_t v) {
         p[i] = v;
 }
 
-__global__ void k_debug_lbsax(const __half *__restrict__ tab, const uint8_t *__restrict__ sax,
-                              int64_t N, int nq, float *__restrict__ out) {
+__global__ void k_debug_lbsax(const float *__restrict__ paa, const float *__restrict__ bp,
+                              const uint8_t *__restrict__ sax, int64_t N, int n, int nq,
+                              float *__restrict__ out) {
+    __shared__ float B[kAlpha + 1];
+    for (int j = threadIdx.x; j <= kAlpha; j += blockDim.x)
+        B[j] = j == 0 ? -INFINITY : (j == kAlpha ? INFINITY : bp[j - 1]);
+    __syncthreads();
+    const float w = (float)(n / kWord);
     for (int q = blockIdx.y; q < nq; q += gridDim.y)
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const __half *tg = tab + (int64_t)q * kWord * kAlpha;
-        float lbs = 0.0f;
-        for (int i = 0; i < kWord; ++i) lbs += __half2float(tg[i * kAlpha + sax[s * kWord + i]]);
+        float lo[kWord], hi[kWord];
+        sax_cells(*reinterpret_cast<const uint4 *>(sax + s * kWord), B, lo, hi);
+        const float *pq = paa + (int64_t)q * 2 * kWord;
+        const float lbs = lb_sax_lower(lo, hi, pq, pq + kWord, w);
         // the scan prunes when lbs > U(1 + 2^-18): the certified value is
         // lbs / (1 + 2^-18) rounded down
         out[(int64_t)q * N + s] = __fdiv_rd(lbs, 1.0f + 0x1p-18f);
@@ -774,7 +797,8 @@ struct ScanConfig {
 };
 
 size_t scan_smem(int G, int n, int p2, bool sax) {
-    return (size_t)G * n * 4 + (sax ? (size_t)G * kWord * kAlpha * 2 : 0) + (size_t)G * kBT * 8 +
+    (void)sax;
+    return (size_t)G * n * 4 + (size_t)G * kBT * 8 +
            (size_t)G * p2 * 8;
 }
 
@@ -1117,7 +1141,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
 
     reserve_common(ws, nq, L, k, pool_C, s);
     ws.qseg.reserve((size_t)nq * idx->S * 2, s);
-    if (!nosax) ws.sax_tab.reserve((size_t)nq * kWord * kAlpha, s);
+    if (!nosax) ws.sax_paa.reserve((size_t)nq * 2 * kWord, s);
     ws.lb.reserve((size_t)nq * L, s);
     ws.approx.reserve((size_t)nq * kAmax, s);
 
@@ -1154,8 +1178,8 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     }
     const int S_tc = o.series_tile > 0 ? o.series_tile : 65536;
     // a1 + a2
-    k_qprep<<<nq, 256, n * sizeof(float), s>>>(Qd, n, idx->seg_ab.p, idx->S, idx->bp.p, ws.qseg.p,
-                                               nosax ? nullptr : reinterpret_cast<__half *>(ws.sax_tab.p));
+    k_qprep<<<nq, 256, n * sizeof(float), s>>>(Qd, n, idx->seg_ab.p, idx->S, ws.qseg.p,
+                                               nosax ? nullptr : ws.sax_paa.p);
     HK_CHECK_LAUNCH();
     k_lb_eapca<<<dim3((unsigned)((L + 127) / 128), std::min(nq, 65535)), 128, 0, s>>>(
         ws.qseg.p, idx->S, idx->leaf_nseg.p, idx->leaf_seg.p, idx->seg_ab.p, idx->env.p, L, nq,
@@ -1175,7 +1199,8 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     a.v = v;
     a.Q = Qd;
     a.nq = nq;
-    a.sax_tab = nosax ? nullptr : reinterpret_cast<const __half *>(ws.sax_tab.p);
+    a.sax_paa = nosax ? nullptr : ws.sax_paa.p;
+    a.bp = idx->bp.p;
     a.qmode = ws.qmode.p;
     a.lb = noprune ? nullptr : ws.lb.p;
     a.U = ws.U.p;
@@ -1672,8 +1697,7 @@ void debug_lb_eapca(hk_index *idx, const float *Qd, int nq, double *out_host) {
     Workspace &ws = idx->ws;
     ws.qseg.reserve((size_t)nq * idx->S * 2, s);
     ws.lb.reserve((size_t)nq * idx->L, s);
-    k_qprep<<<nq, 256, idx->n * sizeof(float), s>>>(Qd, idx->n, idx->seg_ab.p, idx->S, idx->bp.p,
-                                                    ws.qseg.p, nullptr);
+    k_qprep<<<nq, 256, idx->n * sizeof(float), s>>>(Qd, idx->n, idx->seg_ab.p, idx->S, ws.qseg.p, nullptr);
     HK_CHECK_LAUNCH();
     k_lb_eapca<<<dim3((unsigned)((idx->L + 127) / 128), std::min(nq, 65535)), 128, 0, s>>>(
         ws.qseg.p, idx->S, idx->leaf_nseg.p, idx->leaf_seg.p, idx->seg_ab.p, idx->env.p, idx->L, nq,
@@ -1687,13 +1711,13 @@ void debug_lb_eapca(hk_index *idx, const float *Qd, int nq, double *out_host) {
 void debug_lb_sax(hk_index *idx, const float *Qd, int nq, float *out_host) {
     cudaStream_t s = idx->stream;
     Workspace &ws = idx->ws;
-    ws.sax_tab.reserve((size_t)nq * kWord * kAlpha, s);
-    k_qprep<<<nq, 256, idx->n * sizeof(float), s>>>(Qd, idx->n, idx->seg_ab.p, idx->S, idx->bp.p,
-                                                    nullptr, reinterpret_cast<__half *>(ws.sax_tab.p));
+    ws.sax_paa.reserve((size_t)nq * 2 * kWord, s);
+    k_qprep<<<nq, 256, idx->n * sizeof(float), s>>>(Qd, idx->n, idx->seg_ab.p, idx->S, nullptr, ws.sax_paa.p);
     HK_CHECK_LAUNCH();
     DevBuf<float> out;
     out.alloc((size_t)nq * idx->N, s);
-    k_debug_lbsax<<<dim3(256, std::min(nq, 65535)), 256, 0, s>>>(reinterpret_cast<const __half *>(ws.sax_tab.p), idx->sax.p, idx->N, nq, out.p);
+    k_debug_lbsax<<<dim3(256, std::min(nq, 65535)), 256, 0, s>>>(ws.sax_paa.p, idx->bp.p, idx->sax.p, idx->N,
+                                                                  idx->n, nq, out.p);
     HK_CHECK_LAUNCH();
     HK_CHECK_CUDA(cudaMemcpyAsync(out_host, out.p, (size_t)nq * idx->N * sizeof(float),
                                   cudaMemcpyDeviceToHost, s));
