@@ -45,8 +45,9 @@
 namespace hk {
 namespace {
 
-constexpr int kBT = 256;       // scan CTA threads = series per chunk
+constexpr int kBT = 128;       // scan CTA threads = series per chunk
 constexpr int kSlack = 32;     // room for near-ties beyond k in an item list
+constexpr int kRing = 2;       // scan: chunks (2 KB per warp) in flight per warp
 constexpr int kMaxG = 8;
 constexpr int kStatSlots = 24;
 constexpr int kAmax = 256;     // most leaves the approximate step visits
@@ -315,13 +316,41 @@ __global__ void k_leaf_fill(const uint8_t *__restrict__ mask, int nq, uint8_t v,
     }
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only), and its groups.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Packed float32 pairs (the f32x2 pipes): a += (q - x)^2 lane-wise.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void sq_acc2(uint64_t &a, uint64_t q, uint64_t x) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(q), "l"(x));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(a) : "l"(d), "l"(a));
+}
+
 // --------------------------------------------------------------------------
 // a5-a7: the scan.  One CTA per work item at a time (persistent grid).
 template <int G>
-__global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
+__global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.v.n;
-    float *q_s = reinterpret_cast<float *>(smem_raw);                 // G*n
+    float4 *ring_all = reinterpret_cast<float4 *>(smem_raw);          // kBT/32 warps * kRing * 2 KB
+    float *q_s = reinterpret_cast<float *>(ring_all + (kBT / 32) * kRing * 128);   // G*n
     float *stage_d = q_s + G * n;
     int32_t *stage_p = reinterpret_cast<int32_t *>(stage_d + G * kBT);
     float *list_d = reinterpret_cast<float *>(stage_p + G * kBT);     // G*p2
@@ -408,74 +437,109 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
         __syncthreads();
 
         const int64_t s0 = s_s0, s1 = s_s1;
+        // this warp's ring of chunk buffers: chunk c of the warp's 32 series
+        // (16 points each), float4 slot 4*series + (part ^ ((series >> 1) & 3))
+        float4 *ring = ring_all + warp * (kRing * 128);
+        const int nch = n >> 4;
         for (int64_t c0 = s0; c0 < s1; c0 += kBT) {
             const int64_t s = c0 + tid;
-            if (s < s1) {
-                unsigned act = alive_mask;
-                float T[G];
+            const bool valid = s < s1;
+            unsigned act = valid ? alive_mask : 0u;
+            float T[G];
 #pragma unroll
-                for (int g = 0; g < G; ++g) T[g] = s_T[g];
-                if (sax_mask) {
-                    const uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(A.v.sax) + s);
-                    float clo[kWord], chi[kWord];
-                    sax_cells(w4, s_B, clo, chi);
+            for (int g = 0; g < G; ++g) T[g] = s_T[g];
+            if (sax_mask && valid) {
+                const uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(A.v.sax) + s);
+                float clo[kWord], chi[kWord];
+                sax_cells(w4, s_B, clo, chi);
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        if (!(sax_mask >> g & 1)) continue;
-                        const float lbs = lb_sax_lower(clo, chi, s_paa[g], s_paa[g] + kWord, w_sax);
-                        if (lbs > s_Tsax[g]) {
-                            act &= ~(1u << g);
-                            ++my_sax;
-                        }
+                for (int g = 0; g < G; ++g) {
+                    if (!(sax_mask >> g & 1)) continue;
+                    const float lbs = lb_sax_lower(clo, chi, s_paa[g], s_paa[g] + kWord, w_sax);
+                    if (lbs > s_Tsax[g]) {
+                        act &= ~(1u << g);
+                        ++my_sax;
                     }
                 }
-                float acc[G];
+                my_bytes += kWord;
+            }
+            // per query four partial sums, as two packed pairs: the sum runs
+            // as four interleaved chains (any order of the n terms stays
+            // within rho), on the packed float32 pipes
+            uint64_t accA[G], accB[G];
 #pragma unroll
-                for (int g = 0; g < G; ++g) acc[g] = 0.0f;
-                if (sax_mask) my_bytes += kWord;
-                const float4 *xr = reinterpret_cast<const float4 *>(A.v.X + s * n);
-                float4 x0 = __ldg(xr + 0), x1 = __ldg(xr + 1), x2 = __ldg(xr + 2), x3 = __ldg(xr + 3);
-                for (int j = 0; j < n && act; j += 16) {
+            for (int g = 0; g < G; ++g) accA[g] = accB[g] = 0ull;
+            float acc[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[g] = 0.0f;
+            // a6: the warp copies the next chunks of its live series into its
+            // ring (coalesced 64-byte pieces, kRing - 1 ahead) while each lane
+            // works through its own series; a chunk is fetched only for series
+            // that were still live when it was requested
+            const int64_t wbase = c0 + (warp << 5);
+            unsigned need = __ballot_sync(0xffffffffu, act != 0);
+            auto issue = [&](int c) {
+                float4 *slot = ring + (c % kRing) * 128;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int f = lane + 32 * m, sl = f >> 2, part = f & 3;
+                    if (need >> sl & 1)
+                        cp_async16(slot + 4 * sl + (part ^ ((sl >> 1) & 3)),
+                                   A.v.X + (wbase + sl) * n + 16 * c + 4 * part);
+                }
+            };
+#pragma unroll
+            for (int c = 0; c < kRing - 1; ++c) {
+                if (c < nch && need) issue(c);
+                cp_async_commit();
+            }
+            for (int c = 0; c < nch && need; ++c) {
+                if (c + kRing - 1 < nch) issue(c + kRing - 1);
+                cp_async_commit();
+                cp_async_wait<kRing - 1>();
+                __syncwarp();
+                const float4 *slot = ring + (c % kRing) * 128 + 4 * lane;
+                const int sw = (lane >> 1) & 3;
+                const float4 x0 = slot[0 ^ sw], x1 = slot[1 ^ sw], x2 = slot[2 ^ sw], x3 = slot[3 ^ sw];
+                if (act) {
                     my_bytes += 64;
-                    // prefetch the next 16 points while these are consumed
-                    float4 y0 = x0, y1 = x1, y2 = x2, y3 = x3;
-                    if (j + 16 < n) {
-                        y0 = __ldg(xr + (j >> 2) + 4);
-                        y1 = __ldg(xr + (j >> 2) + 5);
-                        y2 = __ldg(xr + (j >> 2) + 6);
-                        y3 = __ldg(xr + (j >> 2) + 7);
-                    }
+                    const int j = c << 4;
+                    const uint64_t X0 = pack2(x0.x, x0.y), X1 = pack2(x0.z, x0.w), X2 = pack2(x1.x, x1.y),
+                                   X3 = pack2(x1.z, x1.w), X4 = pack2(x2.x, x2.y), X5 = pack2(x2.z, x2.w),
+                                   X6 = pack2(x3.x, x3.y), X7 = pack2(x3.z, x3.w);
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         if (!(act >> g & 1)) continue;
                         const float4 *qv = reinterpret_cast<const float4 *>(q_s + g * n + j);
                         const float4 q0 = qv[0], q1 = qv[1], q2 = qv[2], q3 = qv[3];
-                        float a = acc[g], d;
-                        d = q0.x - x0.x; a = fmaf(d, d, a);
-                        d = q0.y - x0.y; a = fmaf(d, d, a);
-                        d = q0.z - x0.z; a = fmaf(d, d, a);
-                        d = q0.w - x0.w; a = fmaf(d, d, a);
-                        d = q1.x - x1.x; a = fmaf(d, d, a);
-                        d = q1.y - x1.y; a = fmaf(d, d, a);
-                        d = q1.z - x1.z; a = fmaf(d, d, a);
-                        d = q1.w - x1.w; a = fmaf(d, d, a);
-                        d = q2.x - x2.x; a = fmaf(d, d, a);
-                        d = q2.y - x2.y; a = fmaf(d, d, a);
-                        d = q2.z - x2.z; a = fmaf(d, d, a);
-                        d = q2.w - x2.w; a = fmaf(d, d, a);
-                        d = q3.x - x3.x; a = fmaf(d, d, a);
-                        d = q3.y - x3.y; a = fmaf(d, d, a);
-                        d = q3.z - x3.z; a = fmaf(d, d, a);
-                        d = q3.w - x3.w; a = fmaf(d, d, a);
-                        acc[g] = a;
+                        uint64_t a = accA[g], b = accB[g];
+                        sq_acc2(a, pack2(q0.x, q0.y), X0);
+                        sq_acc2(b, pack2(q0.z, q0.w), X1);
+                        sq_acc2(a, pack2(q1.x, q1.y), X2);
+                        sq_acc2(b, pack2(q1.z, q1.w), X3);
+                        sq_acc2(a, pack2(q2.x, q2.y), X4);
+                        sq_acc2(b, pack2(q2.z, q2.w), X5);
+                        sq_acc2(a, pack2(q3.x, q3.y), X6);
+                        sq_acc2(b, pack2(q3.z, q3.w), X7);
+                        accA[g] = a;
+                        accB[g] = b;
+                        float a0, a1, b0, b1;
+                        unpack2(a, a0, a1);
+                        unpack2(b, b0, b1);
+                        acc[g] = (a0 + a1) + (b0 + b1);
                         my_pts += 16;
-                        if (a > T[g]) {
+                        if (acc[g] > T[g]) {
                             act &= ~(1u << g);
                             ++my_ab;
                         }
                     }
-                    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
                 }
+                __syncwarp();   // the slot is read by every lane before it is refilled
+                need = __ballot_sync(0xffffffffu, act != 0);
+            }
+            cp_async_wait<0>();   // copies still in flight for series that died
+            __syncwarp();
+            if (valid) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     if (!(act >> g & 1)) continue;
@@ -486,9 +550,9 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
                 }
             }
             __syncthreads();
-            // merge: warp g owns query g's list
-            if (warp < gq && (alive_mask >> warp & 1)) {
-                const int g = warp;
+            // merge: warp w owns the lists of queries w, w + kBT/32, ...
+            for (int g = warp; g < gq; g += kBT / 32) {
+                if (!(alive_mask >> g & 1)) continue;
                 float *ld = list_d + g * A.p2;
                 int32_t *lp = list_p + g * A.p2;
                 const int sc = s_stage[g];
@@ -548,8 +612,8 @@ __global__ void __launch_bounds__(kBT) k_scan(ScanArgs A) {
             __syncthreads();
         }
         // publish: entries at or below T(min(U_item, U_global)), then tighten U
-        if (warp < gq && (alive_mask >> warp & 1)) {
-            const int g = warp;
+        for (int g = warp; g < gq; g += kBT / 32) {
+            if (!(alive_mask >> g & 1)) continue;
             const int q = s_qid[g];
             const float Uf = fminf(s_U[g], __uint_as_float(A.U[q]));
             const float T = __fmul_ru(Uf, 1.0f + rho);
@@ -798,7 +862,7 @@ struct ScanConfig {
 
 size_t scan_smem(int G, int n, int p2, bool sax) {
     (void)sax;
-    return (size_t)G * n * 4 + (size_t)G * kBT * 8 +
+    return (size_t)(kBT / 32) * kRing * 2048 + (size_t)G * n * 4 + (size_t)G * kBT * 8 +
            (size_t)G * p2 * 8;
 }
 
