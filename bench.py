@@ -31,6 +31,8 @@ WORKLOADS = {
     # name: N, n, leaf capacity, total queries, noise sigmas, k, queries per step
     "large": dict(N=100_000_000, n=256, tau=100_000, nq=10_000, sigmas=[0.5, 1.0], k=10, batch=1000,
                   desc="100M random walks x 256, leaf 100K, 10K hard queries (sigma 0.5/1.0), k=10"),
+    "precision": dict(N=10_000_000, n=256, tau=10_000, nq=1024, sigmas=("uniform", 0.01, 1.0), k=100, batch=1024,
+                      desc="10M random walks x 256, leaf 10K, 1024 queries (sigma uniform in [0.01, 1.0]), k=100"),
     "mid": dict(N=10_000_000, n=256, tau=10_000, nq=100, sigmas=[0.01, 0.1, 0.5, 1.0], k=10, batch=100,
                 desc="10M random walks x 256, leaf 10K, 100 queries (sigma 0.01/0.1/0.5/1.0), k=10"),
     # 2-6 GB cases of the large workload's shape, for profiler captures
@@ -158,7 +160,10 @@ def run_reference(args, wl):
     X = workload.random_walk(rows, wl["n"], seed=0, device="cpu").numpy()
     cores = len(os.sched_getaffinity(0))
     nqb = max(1, min(16, cores))
-    Qt, _ = workload.queries(torch.from_numpy(X), nqb * (args.steps + args.warmup), wl["sigmas"], seed=1)
+    sig = wl["sigmas"]
+    if isinstance(sig, tuple) and sig[0] == "uniform":
+        sig = workload.uniform_sigmas(nqb * (args.steps + args.warmup), sig[1], sig[2], seed=1)
+    Qt, _ = workload.queries(torch.from_numpy(X), nqb * (args.steps + args.warmup), sig, seed=1)
     Q = Qt.numpy()
     import oracle
     oracle._lib()
@@ -246,6 +251,109 @@ def serve(binding, idx, Q_all, k, max_batch, qflags, args):
                 max_batch=st["max_batch"], errors=st["errors"])
 
 
+MIX = [  # the served mix: name, N, n, kind, leaf capacity
+    ("20M x 96 Gaussian, L2-normalised", 20_000_000, 96, "gauss_l2", 10_000),
+    ("10M x 128 Gaussian", 10_000_000, 128, "gauss", 10_000),
+    ("10M x 256 random walk", 10_000_000, 256, "rw", 10_000),
+    ("2M x 1024 random walk", 2_000_000, 1024, "rw", 10_000),
+]
+
+
+def serve_mix(args):
+    """Four device-resident collections behind one continuous-batching server:
+    Poisson arrivals at args.serve_mix requests/s, each request a uniformly
+    chosen collection, k uniform in {1, 10, 100}, noise sigma uniform in
+    [0.01, 1.0]; the precision form where a collection has a 16-bit copy
+    (n <= 256), the float32 path otherwise.  Prints one JSON line."""
+    import threading
+    import numpy as np
+    import torch
+    from paper_2212_13297_gb300 import binding, workload
+    import __graft_entry__
+    __graft_entry__.build()
+    rng = np.random.default_rng(2)
+    sv_flags = binding.HK_Q_BF16
+    idxs, pools, builds = [], [], []
+    for ci, (name, N, n, kind, tau) in enumerate(MIX):
+        t0 = time.perf_counter()
+        if kind == "rw":
+            X = workload.random_walk(N, n, seed=10 + ci, device="cuda")
+        else:
+            X = workload.gaussian(N, n, seed=10 + ci, device="cuda", l2=(kind == "gauss_l2"))
+        nqp = 2048
+        sig = workload.uniform_sigmas(nqp, 0.01, 1.0, seed=20 + ci)
+        norm = {"rw": "z", "gauss_l2": "l2", "gauss": None}[kind]
+        Q, _ = workload.queries(X, nqp, sig, seed=20 + ci, norm=norm)
+        flags = binding.HK_BUILD_FP16 if n <= 256 else 0
+        idxs.append(binding.Index(X, tau, flags=flags))
+        pools.append(Q.cpu().numpy())
+        del X
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        builds.append(time.perf_counter() - t0)
+    sv = binding.Server(max_batch=1024, max_wait_us=0, query_flags=sv_flags, workers=2)
+    colls = [sv.add(ix) for ix in idxs]
+    for ci in range(len(MIX)):   # warm each collection's path
+        for t in [sv.submit(colls[ci], pools[ci][i], kk) for i, kk in enumerate((1, 10, 100))]:
+            sv.poll(t, 100, timeout_us=120_000_000)
+    n_req = max(1, int(args.serve_mix * args.serve_seconds))
+    gaps = rng.exponential(1.0 / args.serve_mix, n_req)
+    which = rng.integers(0, len(MIX), n_req)
+    ks = rng.choice([1, 10, 100], n_req)
+    qi = rng.integers(0, 2048, n_req)
+    tickets = [None] * n_req
+    ready = threading.Semaphore(0)
+    lat = np.zeros(n_req)
+    t_done = [0.0]
+
+    def submitter():
+        due = time.perf_counter()
+        for i in range(n_req):
+            due += gaps[i]
+            d = due - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = sv.submit(colls[which[i]], pools[which[i]][qi[i]], int(ks[i]))
+            ready.release()
+
+    def poller():
+        for i in range(n_req):
+            ready.acquire()
+            r = None
+            while r is None:
+                r = sv.poll(tickets[i], int(ks[i]), timeout_us=10_000_000)
+            lat[i] = r[2] / 1e9
+        t_done[0] = time.perf_counter()
+
+    t_start = time.perf_counter()
+    ths = [threading.Thread(target=submitter), threading.Thread(target=poller)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    wall = t_done[0] - t_start
+    st = sv.stats()
+    sv.close()
+
+    def pct(a, p):
+        a = np.sort(a)
+        return float(a[min(len(a) - 1, int(p * len(a)))]) * 1e3 if len(a) else None
+
+    per = []
+    for ci, (name, N, n, kind, tau) in enumerate(MIX):
+        m = which == ci
+        per.append(dict(collection=name, requests=int(m.sum()), p50_ms=pct(lat[m], 0.5), p99_ms=pct(lat[m], 0.99),
+                        form="tensor cores (float16 copy)" if n <= 256 else "float32", build_s=builds[ci]))
+    line = dict(metric="served mix: arrival-to-answer latency, exact k-NN", value=n_req / wall, unit="answers/s",
+                offered_rate=args.serve_mix, requests=n_req, higher_is_better=True, n_gpus=1,
+                latency_ms=dict(p50=pct(lat, 0.5), p99=pct(lat, 0.99), max=float(lat.max()) * 1e3),
+                per_collection=per, batches=st["batches"], mean_batch=st["served"] / max(1, st["batches"]),
+                max_batch=st["max_batch"], errors=st["errors"], data="synthetic",
+                config=dict(workload="served mix: " + "; ".join(m[0] for m in MIX), k=[1, 10, 100],
+                            sigma="uniform [0.01, 1.0]", arrivals="Poisson, seed 2", workers=2))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,6 +375,9 @@ def main():
                     help="also drive the continuous-batching server with Poisson arrivals at this "
                          "rate (requests/s) and report arrival-to-answer latency")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-mix", type=float, default=0.0,
+                    help="instead of the step benchmark, serve the four-collection mix at this "
+                         "rate (requests/s) and print its latency line")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
@@ -274,6 +385,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, wl)
+        return
+    if args.serve_mix > 0:
+        serve_mix(args)
         return
 
     import numpy as np
@@ -293,7 +407,10 @@ def main():
     N, n, k, B = wl["N"], wl["n"], wl["k"], wl["batch"]
     t0 = time.perf_counter()
     X = workload.random_walk(N, n, seed=0, device="cuda")
-    Q_all, _ = workload.queries(X, wl["nq"], wl["sigmas"], seed=1)
+    sig = wl["sigmas"]
+    if isinstance(sig, tuple) and sig[0] == "uniform":
+        sig = workload.uniform_sigmas(wl["nq"], sig[1], sig[2], seed=1)
+    Q_all, _ = workload.queries(X, wl["nq"], sig, seed=1)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     sample = None

@@ -289,6 +289,10 @@ double tc_error_coefficient(int n, int fmt);
 float tc_eb2();
 constexpr int kTcMaxLen = 256;     // longest series the tensor-core form takes
 constexpr int kTcLocalK = 16;     // largest k whose best upper bounds the tensor-core scan tracks
+// Candidate-list and pool length per query in the precision form: its
+// certified band admits the near neighbours around the k-th distance, more
+// of them as k grows (an overflow reruns the query on the float32 path).
+inline int tc_list_cap(int k) { return k * 1024 > 65536 ? k * 1024 : 65536; }
 
 // Exhaustive exact k-NN into caller device buffers using only `sc`.
 void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,

@@ -48,6 +48,7 @@ namespace {
 constexpr int kBT = 128;       // scan CTA threads = series per chunk
 constexpr int kSlack = 32;     // room for near-ties beyond k in an item list
 constexpr int kRing = 2;       // scan: chunks (2 KB per warp) in flight per warp
+constexpr int kRound1Leaves = 8;   // precision form, k > 16: leaves per query in the first round
 constexpr int kMaxG = 8;
 constexpr int kStatSlots = 24;
 constexpr int kAmax = 256;     // most leaves the approximate step visits
@@ -247,6 +248,61 @@ __global__ void k_mask_candidates(const double *__restrict__ lb, int64_t L, int 
     if (cand) {
         mask[t] = 2;
         atomicAdd(&qcand[q], 1);
+    }
+}
+
+// Precision form, k beyond what the tensor-core scan tightens in flight:
+// each query's `r` candidate leaves (mask 2) with the smallest LB_EAPCA go
+// first (mask 3), as in the paper's best-first order of the leaves
+// (Sec. 3.4, Exact-kNN), so that U is exact over many series before the rest.
+__global__ void k_round1_select(const double *__restrict__ lb, int64_t L, int nq, int r,
+                                uint8_t *__restrict__ mask) {
+    __shared__ double bd[32];
+    __shared__ long long bl[32];
+    const int q = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int it = 0; it < r; ++it) {
+        double best = INFINITY;
+        long long bleaf = -1;
+        for (int64_t f = threadIdx.x; f < L; f += blockDim.x) {
+            if (mask[f * nq + q] != 2) continue;
+            const double v = lb[(int64_t)q * L + f];
+            if (bleaf < 0 || v < best || (v == best && f < bleaf)) { best = v; bleaf = f; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const long long ol = __shfl_xor_sync(0xffffffffu, bleaf, o);
+            if (ol >= 0 && (bleaf < 0 || ov < best || (ov == best && ol < bleaf))) { best = ov; bleaf = ol; }
+        }
+        if (lane == 0) { bd[warp] = best; bl[warp] = bleaf; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = INFINITY;
+            long long f = -1;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (bl[w] >= 0 && (f < 0 || bd[w] < b || (bd[w] == b && bl[w] < f))) { b = bd[w]; f = bl[w]; }
+            if (f >= 0) mask[f * nq + q] = 3;
+            bl[0] = f;
+        }
+        __syncthreads();
+        const bool done = bl[0] < 0;
+        __syncthreads();
+        if (done) break;
+    }
+}
+
+// After the first round: candidate leaves (mask 2) whose certified LB now
+// exceeds U drop out.
+__global__ void k_reprune(const double *__restrict__ lb, int64_t L, int nq, const uint32_t *__restrict__ U,
+                          uint8_t *__restrict__ mask, long long *__restrict__ stats) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L * (int64_t)nq) return;
+    if (mask[t] != 2) return;
+    const int64_t leaf = t / nq;
+    const int q = (int)(t % nq);
+    if (lb_lower(lb[(int64_t)q * L + leaf]) > (double)__uint_as_float(U[q])) {
+        mask[t] = 0;
+        stat_add(&stats[ST_LEAVES_CAND], -1);
     }
 }
 
@@ -965,7 +1021,7 @@ void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, 
               uint8_t val, int pool_C, float rho, int stat_pairs, int stat_cands, int stat_bytes,
               cudaStream_t s, ScanTimer *tctimer, bool capture) {
     const int n = idx->n;
-    const int cand_C = std::max(65536, 256 * k);
+    const int cand_C = tc_list_cap(k);
     ws.cand_cnt.reserve(nq, s);
     ws.cand_p.reserve((size_t)nq * cand_C, s);
     ws.cand_lb.reserve((size_t)nq * cand_C, s);
@@ -1201,7 +1257,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     const int S_T = o.series_tile > 0 ? o.series_tile : 8192;
     // the precision form's bound admits a band of near candidates around the
     // k-th distance (a few thousand on hard queries): give its pool room
-    const int pool_C = tc ? std::max(65536, 256 * k) : std::min(65536, std::max(4096, 64 * cfg.cap));
+    const int pool_C = tc ? tc_list_cap(k) : std::min(65536, std::max(4096, 64 * cfg.cap));
 
     reserve_common(ws, nq, L, k, pool_C, s);
     ws.qseg.reserve((size_t)nq * idx->S * 2, s);
@@ -1321,6 +1377,24 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     if (tc) {
         // a9: tensor-core distances with a certified bound, then the exact
         // float32 rescore of the survivors into the pool
+        if (k > kTcLocalK && !noprune) {
+            // the scan cannot lower U in flight for this k: first each
+            // query's best leaves, then U from their exact distances, then
+            // the rest of the candidates against it
+            k_round1_select<<<nq, 256, 0, s>>>(ws.lb.p, L, nq, kRound1Leaves, ws.mask.p);
+            HK_CHECK_LAUNCH();
+            tc_phase(idx, ws, v, Qd, nq, k, S_tc, 3, pool_C, rho, ST_TC_PAIRS, ST_TC_CANDS, ST_TC_BYTES, s,
+                     tctimer, capture);
+            k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
+                                                       (long long *)ws.stats.p, ST_SERIES_CAND, -1);
+            HK_CHECK_LAUNCH();
+            k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+            HK_CHECK_LAUNCH();
+            const int64_t pairs = L * (int64_t)nq;
+            k_reprune<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(ws.lb.p, L, nq, ws.U.p, ws.mask.p,
+                                                                     (long long *)ws.stats.p);
+            HK_CHECK_LAUNCH();
+        }
         tc_phase(idx, ws, v, Qd, nq, k, S_tc, 2, pool_C, rho, ST_TC_PAIRS, ST_TC_CANDS, ST_TC_BYTES, s,
                  tctimer, capture);
     } else {

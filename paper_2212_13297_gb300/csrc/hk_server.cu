@@ -81,7 +81,7 @@ namespace {
 // (pessimistic: precision-form pools and candidate lists included).
 int64_t bytes_per_query(const hk_index *idx, int k) {
     const int64_t L = idx->L, n = idx->n;
-    const int64_t pool = std::max<int64_t>(65536, 256 * (int64_t)k);
+    const int64_t pool = hk::tc_list_cap(k);
     return L * (1 + 4 + 8) + n * 4 * 2 + idx->S * 16 + 16 * 256 * 2 + pool * 16 +
            pool * 8 + 64 * (int64_t)k;
 }
@@ -171,7 +171,9 @@ void worker_loop(hk_server *sv, Worker *w) {
             o.eapca_th = -1.0f;
             o.sax_th = -1.0f;
             o.flags = sv->opts.query_flags & ~(uint32_t)(HK_Q_TIMING | HK_Q_GRAPH);
-            if ((o.flags & HK_Q_BF16) && !idx->has_bf16) o.flags &= ~(uint32_t)HK_Q_BF16;
+            // the precision form where the collection has it (16-bit copy, n <= 256)
+            if ((o.flags & HK_Q_BF16) && (!idx->has_bf16 || idx->n > hk::kTcMaxLen))
+                o.flags &= ~(uint32_t)HK_Q_BF16;
             hk::run_query_ws(idx, w->ws, w->ws_retry, w->Qd.p, nq, k, o, w->stream, w->ids_h,
                              w->dist_h, nullptr);
         } catch (const hk::Error &e) {
