@@ -354,6 +354,47 @@ def serve_mix(args):
     print(json.dumps(line), flush=True)
 
 
+def ablation(args):
+    """The paper's ablation (Sec. 4.2): the float32 path with and without
+    LB_SAX filtering (NoSAX) and the EAPCA_TH / SAX_TH switches (NoThresh),
+    on the mid workload (10M x 256, 100 queries of mixed difficulty, k = 10).
+    Prints one JSON line."""
+    import torch
+    from paper_2212_13297_gb300 import binding, workload
+    import __graft_entry__
+    __graft_entry__.build()
+    wl = WORKLOADS["mid"]
+    X = workload.random_walk(wl["N"], wl["n"], seed=0, device="cuda")
+    Q, _ = workload.queries(X, wl["nq"], wl["sigmas"], seed=1)
+    idx = binding.Index(X, wl["tau"])
+    del X
+    torch.cuda.empty_cache()
+    out = []
+    for name, f in [("Hercules", 0), ("NoSAX", binding.HK_Q_NOSAX), ("NoThresh", binding.HK_Q_NOTHRESH),
+                    ("NoSAX+NoThresh", binding.HK_Q_NOSAX | binding.HK_Q_NOTHRESH)]:
+        for _ in range(args.warmup):
+            idx.query(Q, wl["k"], flags=f)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        agg = {}
+        for _ in range(args.steps):
+            _, _, st = idx.query(Q, wl["k"], flags=f | binding.HK_Q_TIMING)
+            for key, v in st.items():
+                agg[key] = agg.get(key, 0) + v
+        ev1.record()
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        out.append(dict(variant=name, queries_per_s=wl["nq"] * args.steps / t, ms_per_batch=t / args.steps * 1e3,
+                        leaves_candidate_frac=agg["leaves_candidate"] / max(1, agg["leaves_total"]),
+                        sax_pruned_frac=agg["series_sax_pruned"] / max(1, agg["series_candidate"]),
+                        points_per_query=agg["points_computed"] / max(1, agg["queries"]),
+                        skip_sequential=agg["skip_sequential"] / args.steps,
+                        scan_GBps=agg["scan_bytes"] / max(1, agg["scan_ns"])))
+    print(json.dumps(dict(metric="ablation: exact 10-NN queries/s, float32 path", unit="queries/s",
+                          config=dict(workload=wl["desc"]), data="synthetic", variants=out)), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -375,6 +416,8 @@ def main():
                     help="also drive the continuous-batching server with Poisson arrivals at this "
                          "rate (requests/s) and report arrival-to-answer latency")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--ablation", action="store_true",
+                    help="instead of the step benchmark, the NoSAX / NoThresh ablation on the mid workload")
     ap.add_argument("--serve-mix", type=float, default=0.0,
                     help="instead of the step benchmark, serve the four-collection mix at this "
                          "rate (requests/s) and print its latency line")
@@ -388,6 +431,9 @@ def main():
         return
     if args.serve_mix > 0:
         serve_mix(args)
+        return
+    if args.ablation:
+        ablation(args)
         return
 
     import numpy as np

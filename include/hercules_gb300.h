@@ -36,6 +36,7 @@ extern "C" {
 #define HK_ETIMEOUT (-4)  /* a bounded device or host wait ran out           */
 #define HK_EBUSY (-5)     /* the object is in use (server slots full)        */
 #define HK_EINTERNAL (-6) /* an internal consistency check failed            */
+#define HK_EIO (-7)       /* a file could not be opened, read or written     */
 
 #define HK_ISAX_SEGMENTS 16   /* iSAX word length (Sec. 2)                     */
 #define HK_ISAX_ALPHABET 256  /* iSAX alphabet (Sec. 2)                        */
@@ -93,6 +94,26 @@ typedef struct {
 } hk_index_info;
 
 int hk_index_info_get(const hk_index *idx, hk_index_info *out);
+
+/*
+ * hk_save -- write the index to the file at path (created or truncated): the
+ * tree's leaf synopses and segmentations, the leaf-ordered raw series, their
+ * positions' original ids and iSAX words, and the 16-bit copy when the index
+ * has one -- the paper's HTree, LRDFile and LSDFile (Sec. 3.3) in one file.
+ * Layout: the tag "HKIDX001", a header of sizes, then each array as a 64-bit
+ * byte count followed by its bytes, then an FNV-1a 64-bit checksum of all
+ * array bytes; integers and floats in this machine's byte order.  Returns
+ * HK_EIO if the file cannot be written.  The index is not modified.
+ *
+ * hk_load -- read a file written by hk_save into a new index (device memory
+ * allocated on the current device, copies on `stream`); *out as for
+ * hk_build.  A file that does not start with the tag, whose header is
+ * inconsistent, whose arrays have the wrong lengths or whose checksum does
+ * not match returns HK_EINVAL with nothing allocated; an unreadable file
+ * returns HK_EIO.  Answers from the loaded index equal the saved index's.
+ */
+int hk_save(const hk_index *idx, const char *path);
+int hk_load(const char *path, void *stream, hk_index **out);
 
 /* Query flags. */
 #define HK_Q_NOSAX 1u      /* skip LB_SAX filtering (ablation, Sec. 4.2)      */

@@ -22,6 +22,7 @@ HK_ECUDA = -3
 HK_ETIMEOUT = -4
 HK_EBUSY = -5
 HK_EINTERNAL = -6
+HK_EIO = -7
 
 HK_BUILD_ADOPT = 1
 HK_BUILD_BF16 = 2
@@ -94,7 +95,7 @@ EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_scan_knn"
            "hk_scan_knn_noalloc",
            "hk_isax_breakpoints", "hk_index_export", "hk_debug_lb_eapca", "hk_debug_lb_sax",
            "hk_debug_tc_dist", "hk_server_create", "hk_server_add", "hk_submit", "hk_poll",
-           "hk_server_stats_get", "hk_server_destroy", "hk_tune",
+           "hk_server_stats_get", "hk_server_destroy", "hk_tune", "hk_save", "hk_load",
            "hk_last_error", "hk_version"]
 
 
@@ -134,6 +135,8 @@ def lib():
         L.hk_server_destroy.argtypes = [vp]
         L.hk_tune.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, vp,
                               ctypes.POINTER(hk_tune_result)]
+        L.hk_save.argtypes = [vp, ctypes.c_char_p]
+        L.hk_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
         L.hk_last_error.restype = ctypes.c_char_p
         L.hk_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -207,6 +210,21 @@ class Index:
             self.close()
         except Exception:
             pass
+
+    def save(self, path):
+        """hk_save: write the index to a file."""
+        _check(lib().hk_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """hk_load: an index read from a file written by save()."""
+        h = ctypes.c_void_p()
+        _check(lib().hk_load(os.fsencode(path), _stream(stream), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self._h = h
+        i = self.info()
+        self.N, self.n = i["N"], i["n"]
+        return self
 
     def info(self):
         i = hk_index_info()
