@@ -132,20 +132,23 @@ def dist_env():
 
 def cpu_oracle_rate(X_sample, Q, N_full, budget_s=10.0, chunk=250_000):
     """Oracle queries/s over a collection of N_full series, extrapolated from
-    the time it takes to scan a sample of rows for len(Q) queries."""
+    the time the oracle takes to scan the sample rows for blocks of queries
+    (Q's rows, block after block, until about budget_s of CPU time)."""
     import oracle
-    s = oracle.KnnStream(Q, 10)
-    done = 0
+    nb = max(1, min(16, Q.shape[0]))
     t0 = time.perf_counter()
-    while done < X_sample.shape[0]:
-        blk = X_sample[done:done + chunk]
-        s.update(blk, done)
-        done += blk.shape[0]
+    queries = 0
+    while True:
+        qb = Q[(queries % Q.shape[0]):(queries % Q.shape[0]) + nb]
+        s = oracle.KnnStream(qb, 10)
+        for done in range(0, X_sample.shape[0], chunk):
+            s.update(X_sample[done:done + chunk], done)
+        queries += qb.shape[0]
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    qps = Q.shape[0] / (dt * (N_full / done))
-    return qps, dt, done, s.nthreads
+    qps = queries / (dt * (N_full / X_sample.shape[0]))
+    return qps, dt, X_sample.shape[0], s.nthreads, queries
 
 
 def run_reference(args, wl):
@@ -409,7 +412,9 @@ def main():
     ap.add_argument("--series-tile", type=int, default=0)
     ap.add_argument("--l-max", type=int, default=0)
     ap.add_argument("--plain-steps", type=int, default=2,
-                    help="steps of the float32 path measured beside a tensor-core form")
+                    help="steps of the float32 path measured beside the headline form")
+    ap.add_argument("--plain-groups", default="0,4",
+                    help="query groups of the float32 measurements (0 = the library's choice)")
     ap.add_argument("--form", default="fp16", choices=["plain", "bf16", "fp16"],
                     help="plain float32 scan, or the tensor-core form on a bfloat16 / float16 copy")
     ap.add_argument("--serve", type=float, default=0.0,
@@ -478,10 +483,11 @@ def main():
     dist_out = torch.empty((B, k), dtype=torch.float32, device="cuda")
     qkw = dict(l_max=args.l_max, query_group=args.query_group, series_tile=args.series_tile)
 
-    def timed(flags, steps, warmup, first):
+    def timed(flags, steps, warmup, first, **over):
         """Device time of `steps` batches (after `warmup`), summed stats, per-step latencies."""
+        kw = dict(qkw, **over)
         for i in range(warmup):
-            idx.query(batches[(first + i) % len(batches)], k, flags=flags, out=(ids, dist_out), **qkw)
+            idx.query(batches[(first + i) % len(batches)], k, flags=flags, out=(ids, dist_out), **kw)
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
@@ -494,7 +500,7 @@ def main():
         for i in range(steps):
             ts = time.perf_counter()
             _, _, st = idx.query(batches[(first + warmup + i) % len(batches)], k, flags=flags,
-                                 out=(ids, dist_out), **qkw)
+                                 out=(ids, dist_out), **kw)
             lat.append(time.perf_counter() - ts)
             for key, v in st.items():
                 agg[key] = agg.get(key, 0) + v
@@ -536,13 +542,20 @@ def main():
         e2e = dict(value=ws * B * args.steps / t_e2e, unit="queries/s",
                    h2d_bytes_per_step=B * n * 4, d2h_bytes_per_step=B * k * 12)
 
-    # the plain float32 path on the same index, for comparison
+    # the plain float32 path on the same index, for comparison, at each query
+    # group asked for (0 = the library's choice): more queries per series read
+    # means fewer bytes per query but more arithmetic per byte
     forms = {args.form: dict(value=value, ms_per_step=t_dev / args.steps * 1e3)}
-    plain = None
-    if args.form != "plain" and args.plain_steps > 0:
-        tp, aggp, _ = timed(binding.HK_Q_TIMING, args.plain_steps, 1, args.warmup)
-        forms["plain"] = dict(value=ws * B * args.plain_steps / tp, ms_per_step=tp / args.plain_steps * 1e3)
-        plain = aggp
+    plain_runs = []
+    if args.plain_steps > 0:
+        for gsz in [int(x) for x in args.plain_groups.split(",") if x.strip()]:
+            if args.form == "plain" and gsz == args.query_group:
+                continue   # the headline run already is this one
+            tp, aggp, _ = timed(binding.HK_Q_TIMING, args.plain_steps, 1, args.warmup, query_group=gsz)
+            name = "plain" if gsz == 0 else "plain_group%d" % gsz
+            forms[name] = dict(value=ws * B * args.plain_steps / tp, ms_per_step=tp / args.plain_steps * 1e3,
+                               query_group=gsz or "auto (8)")
+            plain_runs.append((name, aggp))
 
     serving = serve(binding, idx, Q_all, k, B, qflags & ~binding.HK_Q_TIMING, args) \
         if args.serve > 0 else None
@@ -574,6 +587,8 @@ def main():
                         frac=pr["hbm"]["frac"], traffic=None, kernel="k_scan",
                         peak_note="of measured (%s)" % pk["source"])
         roof["kernel_share_of_step"] = agg["scan_ns"] / 1e9 / t_dev
+        for name, a in plain_runs:
+            roof[name + "_k_scan"] = plain_roof(a)
     else:
         tc_s = agg["tc_ns"] / 1e9
         flops = 2.0 * n * agg["tc_pairs"]
@@ -599,17 +614,17 @@ def main():
                 traffic=dram["approx"] if dram else None,
                 note="the same kernel on each query's approximate-search leaves (few queries per "
                      "leaf: bound by the 16-bit rows it streams, not by the MMA)")
-        if plain:
-            roof["plain_k_scan"] = plain_roof(plain)
+        for name, a in plain_runs:
+            roof[name + "_k_scan"] = plain_roof(a)
 
     cpu = None
     if sample is not None:
         cores = len(os.sched_getaffinity(0))
         nqb = max(1, min(16, cores))
-        qps, dt, rows, thr = cpu_oracle_rate(sample, Q_all[:nqb].cpu().numpy(), N)
+        qps, dt, rows, thr, nqs = cpu_oracle_rate(sample, Q_all[:256].cpu().numpy(), N)
         cpu = dict(value=qps, unit="queries/s", cores=thr, kind="oracle",
-                   sample="%d queries x first %d series (%.1f s of CPU), time scaled to %d series"
-                          % (nqb, rows, dt, N))
+                   sample="%d queries (blocks of %d) x first %d series (%.1f s of CPU), time scaled to "
+                          "%d series" % (nqs, nqb, rows, dt, N))
 
     lat = sorted(step_lat)
     dtype = {"plain": "f32", "bf16": "bf16", "fp16": "fp16"}[args.form]
