@@ -130,6 +130,12 @@ def dist_env():
     return ws, rank, local
 
 
+def metric_name(wl):
+    N, n, k = wl["N"], wl["n"], wl["k"]
+    size = "%dM x %d" % (N // 1_000_000, n) if N >= 1_000_000 else "%d x %d" % (N, n)
+    return "exact %d-NN queries/s (%s)" % (k, size)
+
+
 def cpu_oracle_rate(X_sample, Q, N_full, budget_s=10.0, chunk=250_000):
     """Oracle queries/s over a collection of N_full series, extrapolated from
     the time the oracle takes to scan the sample rows for blocks of queries
@@ -159,7 +165,7 @@ def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    rows = 1_000_000
+    rows = min(250_000, wl["N"])   # rows scanned per step (the collection's first rows)
     X = workload.random_walk(rows, wl["n"], seed=0, device="cpu").numpy()
     cores = len(os.sched_getaffinity(0))
     nqb = max(1, min(16, cores))
@@ -175,22 +181,22 @@ def run_reference(args, wl):
         q = Q[i * nqb:(i + 1) * nqb]
         t0 = time.perf_counter()
         s = oracle.KnnStream(q, wl["k"], nthreads=cores)
-        s.update(X[:250_000], 0)
+        s.update(X, 0)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
-    # one step = nqb queries over 250K rows; scale to the full collection
-    scale = wl["N"] / 250_000
+    # one step = nqb queries over `rows` rows; scale to the full collection
+    scale = wl["N"] / rows
     per_step = statistics.mean(times) * scale
     value = nqb / per_step
-    line = dict(impl="reference", metric="exact %d-NN queries/s" % wl["k"], value=value,
+    line = dict(impl="reference", metric=metric_name(wl), value=value,
                 unit="queries/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
                 ms_per_step=per_step * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=wl["desc"], N=wl["N"], n=wl["n"], k=wl["k"]),
                 cpu_baseline=dict(value=value, unit="queries/s", cores=cores, kind="oracle",
-                                  sample="%d queries x 250,000 of the series per step, "
-                                         "time scaled by %.0fx to %d series" % (nqb, scale, wl["N"])),
+                                  sample="%d queries x %d of the series per step, "
+                                         "time scaled by %.0fx to %d series" % (nqb, rows, scale, wl["N"])),
                 e2e=dict(value=value, unit="queries/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -629,7 +635,7 @@ def main():
     lat = sorted(step_lat)
     dtype = {"plain": "f32", "bf16": "bf16", "fp16": "fp16"}[args.form]
     line = dict(
-        metric="exact %d-NN queries/s (%s)" % (k, "%dM x %d" % (N // 1_000_000, n) if N >= 1_000_000 else "%d x %d" % (N, n)),
+        metric=metric_name(wl),
         value=value, unit="queries/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
         ms_per_step=t_dev / args.steps * 1e3, higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype=dtype, data="synthetic",
