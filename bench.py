@@ -603,8 +603,8 @@ def main():
         dram = DRAM_TRAFFIC.get((args.workload, args.form))
         roof = dict(bound="tensor", achieved=ach, peak=peak_t, unit="TFLOP/s", frac=(ach or 0) / peak_t,
                     traffic=dram["exact"] if dram else None, kernel="k_tc_scan",
-                    traffic_note=("DRAM bytes per exact-step launch (%s); algorithmic: the candidate "
-                                  "leaves' 16-bit rows once, about 25 GB" % dram["source"]) if dram else None,
+                    traffic_note=("DRAM bytes per exact-step launch (%s)" % dram["source"]) if dram else None,
+                    algorithmic_dram_bytes_per_launch=agg.get("tc_leaf_bytes", 0) / args.steps,
                     peak_note="of measured sustained bf16 (%s); %s dense rate equals bf16's nominally; "
                               "2n flops per (query, series) pair" % (pk["source"], args.form),
                     frac_of_burst=(ach or 0) / (pk.get("bf16_tflops") or 1920.7),

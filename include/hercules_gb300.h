@@ -172,6 +172,9 @@ typedef struct {
                                      cores (k <= 16; tc_* count the exact step)  */
     int64_t tc_approx_ns;         /* its kernel time (HK_Q_TIMING), ns           */
     int64_t tc_approx_bytes;      /* its 16-bit rows and norms copied in         */
+    int64_t tc_leaf_bytes;        /* 16-bit rows and norms of the leaves the exact
+                                     step scans, each leaf once: the least DRAM
+                                     traffic that step can have                  */
 } hk_query_stats;
 
 /*

@@ -52,7 +52,7 @@ class hk_query_stats(ctypes.Structure):
         "series_sax_pruned", "series_abandoned", "series_full", "points_computed", "rescored",
         "fallback_queries", "retried_queries", "work_items", "skip_sequential", "scan_ns", "kernel_launches",
         "scan_bytes", "tc_pairs", "tc_candidates", "tc_ns", "tc_bytes", "tc_approx_pairs",
-        "tc_approx_ns", "tc_approx_bytes")]
+        "tc_approx_ns", "tc_approx_bytes", "tc_leaf_bytes")]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}

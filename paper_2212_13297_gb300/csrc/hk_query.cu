@@ -57,7 +57,7 @@ enum StatIdx {
     ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_APPROX, ST_LEAVES_CAND, ST_SERIES_CAND,
     ST_SAX_PRUNED, ST_ABANDONED, ST_FULL, ST_POINTS, ST_RESCORED, ST_FALLBACK,
     ST_ITEMS, ST_SKIPSEQ, ST_SCAN_NS, ST_LAUNCHES, ST_SCAN_BYTES, ST_RETRIED, ST_TC_PAIRS,
-    ST_TC_CANDS, ST_TC_BYTES, ST_TCA_PAIRS, ST_TCA_CANDS, ST_TCA_BYTES, ST_COUNT
+    ST_TC_CANDS, ST_TC_BYTES, ST_TCA_PAIRS, ST_TCA_CANDS, ST_TCA_BYTES, ST_TC_LEAF_BYTES, ST_COUNT
 };
 static_assert(ST_COUNT <= kStatSlots, "stat slots");
 
@@ -1206,6 +1206,7 @@ void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s, Scan
     stats->tc_bytes = st[ST_TC_BYTES];
     stats->tc_approx_pairs = st[ST_TCA_PAIRS];
     stats->tc_approx_bytes = st[ST_TCA_BYTES];
+    stats->tc_leaf_bytes = st[ST_TC_LEAF_BYTES];
     stats->scan_ns = timer ? timer->total_ns() : 0;
     stats->kernel_launches = launches;
 }
@@ -1231,6 +1232,18 @@ __global__ void k_count_items_and_series(const int64_t *__restrict__ item_off, i
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
         stat_add(&stats[ST_ITEMS], item_off[L]);
+}
+
+// The exact tensor-core step's algorithmic DRAM bytes: the 16-bit rows and
+// norms of every leaf some query of the batch scans, each counted once.
+__global__ void k_tc_leaf_bytes(const int32_t *__restrict__ qcnt, const int64_t *__restrict__ leaf_off,
+                                int64_t L, int n, long long *__restrict__ stats, int slot) {
+    long long b = 0;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < L;
+         f += (int64_t)gridDim.x * blockDim.x)
+        if (qcnt[f] > 0) b += (leaf_off[f + 1] - leaf_off[f]) * (long long)(2 * n + 8);
+    b = warp_sum_ll(b);
+    if ((threadIdx.x & 31) == 0 && b) stat_add(&stats[slot], b);
 }
 
 }  // namespace
@@ -1397,6 +1410,9 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         }
         tc_phase(idx, ws, v, Qd, nq, k, S_tc, 2, pool_C, rho, ST_TC_PAIRS, ST_TC_CANDS, ST_TC_BYTES, s,
                  tctimer, capture);
+        k_tc_leaf_bytes<<<8, 256, 0, s>>>(ws.leaf_qcnt.p, idx->leaf_off.p, L, n, (long long *)ws.stats.p,
+                                          ST_TC_LEAF_BYTES);
+        HK_CHECK_LAUNCH();
     } else {
         scan_phase(ws, v, a, cfg, 2, nq, s, timer);
     }
