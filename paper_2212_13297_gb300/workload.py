@@ -34,18 +34,25 @@ def _l2norm_(x: torch.Tensor) -> torch.Tensor:
     return x
 
 
-def random_walk(N: int, n: int, seed: int = 0, device="cpu", out=None):
-    """N z-normalised random walks of length n, float32 [N, n]."""
+def random_walk_chunks(N: int, n: int, seed: int = 0, device="cpu"):
+    """The rows of random_walk(N, n, seed) as (first row, float32 block) pairs,
+    generated block by block from the same random stream."""
     dev = torch.device(device)
-    if out is None:
-        out = torch.empty((N, n), dtype=torch.float32, device=dev)
     g = torch.Generator(device=dev)
     g.manual_seed(seed)
     for a in range(0, N, CHUNK_ROWS):
         b = min(N, a + CHUNK_ROWS)
         steps = torch.randn((b - a, n), generator=g, device=dev, dtype=torch.float32)
         walk = torch.cumsum(steps.double(), dim=1)
-        out[a:b] = _znorm_(walk).float()
+        yield a, _znorm_(walk).float()
+
+
+def random_walk(N: int, n: int, seed: int = 0, device="cpu", out=None):
+    """N z-normalised random walks of length n, float32 [N, n]."""
+    if out is None:
+        out = torch.empty((N, n), dtype=torch.float32, device=torch.device(device))
+    for a, rows in random_walk_chunks(N, n, seed, device):
+        out[a:a + rows.shape[0]] = rows
     return out
 
 
