@@ -2,6 +2,13 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
+Parity unpinned for the split policy: the paper leaves getBestSplitPolicy to
+DSTree, so which split a node takes is this project's reading (below); what
+the paper fixes -- the threshold rule of its worked example, children that
+partition their parent, synopses that enclose their members, inorder leaf
+order -- is pinned by tests.  Exact answers do not depend on the policy: any
+valid tree gives the same k nearest neighbours.
+
 Series are inserted one at a time in id order, as Algorithm InsertSeriesToNode
 does for a single insert worker: route to a leaf through the split policies of
 the internal nodes, append, and split the leaf once it holds more than tau
