@@ -130,6 +130,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(t, ws):
+    """The largest of each rank's t (the job's time): one all-reduce over the
+    default process group (NCCL tensors on the GPU, gloo on the CPU)."""
+    if ws <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def rank_batch(i, rank, nbatches):
+    """The query batch rank `rank` answers at step i: replicas answer
+    different batches (weak scaling: each rank adds its own queries)."""
+    return (i + rank) % nbatches
+
+
 def metric_name(wl):
     N, n, k = wl["N"], wl["n"], wl["k"]
     size = "%dM x %d" % (N // 1_000_000, n) if N >= 1_000_000 else "%d x %d" % (N, n)
@@ -493,7 +512,8 @@ def main():
         """Device time of `steps` batches (after `warmup`), summed stats, per-step latencies."""
         kw = dict(qkw, **over)
         for i in range(warmup):
-            idx.query(batches[(first + i) % len(batches)], k, flags=flags, out=(ids, dist_out), **kw)
+            idx.query(batches[rank_batch(first + i, rank, len(batches))], k, flags=flags,
+                      out=(ids, dist_out), **kw)
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
@@ -505,8 +525,8 @@ def main():
         lat, agg = [], {}
         for i in range(steps):
             ts = time.perf_counter()
-            _, _, st = idx.query(batches[(first + warmup + i) % len(batches)], k, flags=flags,
-                                 out=(ids, dist_out), **kw)
+            _, _, st = idx.query(batches[rank_batch(first + warmup + i, rank, len(batches))], k,
+                                 flags=flags, out=(ids, dist_out), **kw)
             lat.append(time.perf_counter() - ts)
             for key, v in st.items():
                 agg[key] = agg.get(key, 0) + v
@@ -514,11 +534,7 @@ def main():
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-        t = ev0.elapsed_time(ev1) / 1e3
-        if ws > 1:
-            tt = torch.tensor([t], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws)
         return t, agg, lat
 
     sampler = ClockSampler(dev_index)
@@ -531,7 +547,8 @@ def main():
     # host results out; the copies are inside each call)
     e2e = None
     if not args.no_e2e:
-        hq = [batches[args.warmup + i].cpu().pin_memory() for i in range(args.steps)]
+        hq = [batches[rank_batch(args.warmup + i, rank, len(batches))].cpu().pin_memory()
+              for i in range(args.steps)]
         hid = np.empty((B, k), np.int64)
         hdi = np.empty((B, k), np.float32)
         torch.cuda.synchronize()
@@ -540,11 +557,7 @@ def main():
         te = time.perf_counter()
         for i in range(args.steps):
             idx.query(hq[i], k, flags=qflags & ~binding.HK_Q_TIMING, out=(hid, hdi), **qkw)
-        t_e2e = time.perf_counter() - te
-        if ws > 1:
-            t = torch.tensor([t_e2e], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(time.perf_counter() - te, ws)
         e2e = dict(value=ws * B * args.steps / t_e2e, unit="queries/s",
                    h2d_bytes_per_step=B * n * 4, d2h_bytes_per_step=B * k * 12)
 
