@@ -29,8 +29,10 @@
 // float32 distance exceeds T(U) = U(1+rho) rounded up.  The final step
 // recomputes in binary64 every pooled candidate at or below T(U_final) and
 // ranks them by (binary64 distance, id).  If a list or pool overflows (more
-// near-ties than it holds), that query is redone by an exhaustive collection
-// of every series at or below T(U_final).
+// near-ties than it holds), that query is answered again on the float32 path
+// starting from its final bound (tight, so few candidates qualify); if that
+// overflows too, every series at or below T(U_final) is collected
+// exhaustively.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -4,8 +4,8 @@
 // more bits of precision for collections inside float16's range).
 //
 // For a block of up to 128 queries and a run of series, D~(q,x) =
-// |q|^2 + |x|^2 - 2 q^.x^ with q^, x^ the bfloat16 roundings and the dot
-// products accumulated in float32 in tensor memory.  Each D~ carries a
+// |q|^2 + |x|^2 - 2 q^.x^ with the dot products of the 16-bit roundings q^,
+// x^ accumulated in float32 in tensor memory.  Each D~ carries a
 // certified error bound E(q,x) = A_q |x| + B (|q|^2 + |x|^2):
 //   |q^.x^ - q.x| <= (2u + u^2 + g(1+u)^2) |q||x| + (subnormal term),
 //   u = 2^-8 (bfloat16) or 2^-11 (float16),
@@ -18,7 +18,7 @@
 // keeps its k smallest D~ + E and tightens U with them.  Candidates are
 // rescored exactly afterwards, so the answer stays exact.
 //
-// Data layout.  The bfloat16 copy of the collection is stored in the
+// Data layout.  The 16-bit copy of the collection is stored in the
 // tensor core's no-swizzle K-major "core matrix" order: series are grouped
 // by 8 (leaf order); a group is n/8 blocks of 8 series x 8 points (128 bytes),
 // block k holding points 8k..8k+7.  A tile of 128 consecutive series (16
@@ -30,12 +30,13 @@
 // points per 32-bit column), so each MMA reads only the series tile from
 // shared memory.
 //
-// CTA roles (18 warps): warp 0 issues the bulk copies (a whole series tile
-// and its norm pairs per stage), warp 1 (one thread) issues tcgen05.mma and
-// tcgen05.commit, warps 2-17 write the query block into tensor memory at the
-// start of each item, then read the accumulators with tcgen05.ld and
-// filter: warp w reads TMEM lane quarter w%4 (query rows 32(w%4)..+31) and a
-// quarter of the tile's columns.  Per element the filter is two FMAs and a
+// CTA roles (10 warps): warp 0 claims work items (a 32-way search over the
+// item offsets) and, from one thread, issues the bulk copies (a whole series
+// tile and its norm pairs per stage); warp 1 (one thread) issues tcgen05.mma
+// and tcgen05.commit; warps 2-9 write the query block into tensor memory at
+// the start of each item, then read the accumulators with tcgen05.ld and
+// filter: warp w reads TMEM lane quarter w%4 (query rows 32(w%4)..+31) and
+// half of the tile's columns.  Per element the filter is two FMAs and a
 // minimum; the per-column test and the exact bounds are formed only when a
 // minimum reaches the row's threshold.
 // Three shared-memory stages for series tiles, three TMEM accumulators.  Every
@@ -75,7 +76,7 @@ static_assert(kNormSlots >= kTcStages + kAcc + 1, "norm slot reuse distance");
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far above any legitimate wait
 constexpr int kLocalK = kTcLocalK;   // k-best upper bounds kept per epilogue thread
 constexpr double kTcEb = 0x1p-19;   // relative term for norm and epilogue rounding
-constexpr float kF16Max = 65504.0f;      // 2k up to this tightens U per row
+constexpr float kF16Max = 65504.0f;      // largest finite float16: the float16 copy's range
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
