@@ -37,7 +37,7 @@ def _oracle_stream(N, n, seed, Qs, k):
 
 
 # name: N, n, leaf capacity, batch, sigmas, ks, form, sampled rows of the batch
-CONFIGS = {
+SIZES = {
     "large": (100_000_000, 256, 100_000, 1000, [0.5, 1.0], [10], "fp16", [0, 333, 666, 999]),
     "mid": (10_000_000, 256, 10_000, 100, [0.01, 0.1, 0.5, 1.0], [1, 10], "plain", [0, 13, 26, 39, 52, 65, 78, 99]),
     "precision": (10_000_000, 256, 10_000, 1024, "uniform", [100], "fp16", [0, 511, 1023]),
@@ -46,7 +46,7 @@ CONFIGS = {
 
 @pytest.mark.parametrize("name", ["mid", "precision", "large"])
 def test_full_size_sample_matches_oracle(hb, oracle_lib, name):
-    N, n, tau, B, sig, ks, form, sample = CONFIGS[name]
+    N, n, tau, B, sig, ks, form, sample = SIZES[name]
     wl = _wl()
     free, total = torch.cuda.mem_get_info()
     need = N * n * 4 * 2.6 if form == "fp16" else N * n * 4 * 2.1
