@@ -395,6 +395,16 @@ __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
 __device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
+__device__ __forceinline__ uint64_t sub_rd2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sqacc_rd2(uint64_t d, uint64_t acc) {
+    uint64_t r;
+    asm("fma.rm.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(acc));
+    return r;
+}
 __device__ __forceinline__ void sq_acc2(uint64_t &a, uint64_t q, uint64_t x) {
     uint64_t d;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(q), "l"(x));
@@ -424,6 +434,7 @@ __global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
     __shared__ long long s_cnt[4];   // sax pruned, abandoned, full, points
     __shared__ float s_B[kAlpha + 1];          // cell ends: -inf, breakpoints, +inf
     __shared__ float s_paa[G][2 * kWord];      // per query: PAA rounded down, then up
+    __shared__ float4 s_pp[(G + 1) / 2][kWord]; // per query pair: (down g, down g+1, up g, up g+1)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t total = A.item_off[A.v.L];
@@ -493,6 +504,15 @@ __global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
                 s_paa[g][tid] = A.sax_paa[(int64_t)s_qid[g] * 2 * kWord + tid];
         }
         __syncthreads();
+        if (G > 1 && tid < kWord) {
+            for (int pr = 0; pr < G / 2; ++pr) {
+                const int g0 = 2 * pr, g1 = 2 * pr + 1;
+                const bool u0 = sax_mask >> g0 & 1, u1 = sax_mask >> g1 & 1;
+                s_pp[pr][tid] = make_float4(u0 ? s_paa[g0][tid] : 0.f, u1 ? s_paa[g1][tid] : 0.f,
+                                            u0 ? s_paa[g0][kWord + tid] : 0.f, u1 ? s_paa[g1][kWord + tid] : 0.f);
+            }
+        }
+        __syncthreads();
 
         const int64_t s0 = s_s0, s1 = s_s1;
         // this warp's ring of chunk buffers: chunk c of the warp's 32 series
@@ -510,13 +530,40 @@ __global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
                 const uint4 w4 = __ldg(reinterpret_cast<const uint4 *>(A.v.sax) + s);
                 float clo[kWord], chi[kWord];
                 sax_cells(w4, s_B, clo, chi);
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    if (!(sax_mask >> g & 1)) continue;
-                    const float lbs = lb_sax_lower(clo, chi, s_paa[g], s_paa[g] + kWord, w_sax);
-                    if (lbs > s_Tsax[g]) {
-                        act &= ~(1u << g);
+                if (G == 1) {
+                    const float lbs = lb_sax_lower(clo, chi, s_paa[0], s_paa[0] + kWord, w_sax);
+                    if (lbs > s_Tsax[0]) {
+                        act &= ~1u;
                         ++my_sax;
+                    }
+                } else {
+                    // two queries per packed instruction, the same rounded-down
+                    // steps as lb_sax_lower
+#pragma unroll
+                    for (int pr = 0; pr < G / 2; ++pr) {
+                        const unsigned pm = (sax_mask >> (2 * pr)) & 3u;
+                        if (!pm) continue;
+                        uint64_t acc2 = 0ull;
+#pragma unroll
+                        for (int i = 0; i < kWord; ++i) {
+                            const float4 v = s_pp[pr][i];
+                            const uint64_t a2 = sub_rd2(pack2(clo[i], clo[i]), pack2(v.z, v.w));
+                            const uint64_t b2 = sub_rd2(pack2(v.x, v.y), pack2(chi[i], chi[i]));
+                            float a0, a1, b0, b1;
+                            unpack2(a2, a0, a1);
+                            unpack2(b2, b0, b1);
+                            acc2 = sqacc_rd2(pack2(fmaxf(fmaxf(a0, b0), 0.0f), fmaxf(fmaxf(a1, b1), 0.0f)), acc2);
+                        }
+                        float l0, l1;
+                        unpack2(acc2, l0, l1);
+                        if ((pm & 1u) && __fmul_rd(l0, w_sax) > s_Tsax[2 * pr]) {
+                            act &= ~(1u << (2 * pr));
+                            ++my_sax;
+                        }
+                        if ((pm & 2u) && __fmul_rd(l1, w_sax) > s_Tsax[2 * pr + 1]) {
+                            act &= ~(1u << (2 * pr + 1));
+                            ++my_sax;
+                        }
                     }
                 }
                 my_bytes += kWord;
