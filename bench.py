@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # name: N, n, leaf capacity, total queries, noise sigmas, k, queries per step
-    "large": dict(N=100_000_000, n=256, tau=100_000, nq=10_000, sigmas=[0.5, 1.0], k=10, batch=1000,
+    "large": dict(N=100_000_000, n=256, tau=100_000, nq=10_000, sigmas=[0.5, 1.0], k=10, batch=2000,
                   desc="100M random walks x 256, leaf 100K, 10K hard queries (sigma 0.5/1.0), k=10"),
     "precision": dict(N=10_000_000, n=256, tau=10_000, nq=1024, sigmas=("uniform", 0.01, 1.0), k=100, batch=1024,
                       desc="10M random walks x 256, leaf 10K, 1024 queries (sigma uniform in [0.01, 1.0]), k=100"),
@@ -49,8 +49,9 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
 # capture committed under profiles/ (named beside each entry); a workload or
 # form without one reports traffic null.  Re-take them when the kernel changes.
-DRAM_TRAFFIC = {
-    ("large", "fp16"): dict(exact=69.32e9, approx=16.60e9, source="profiles/k_tc_scan_dram_100M_x256_fp16.md"),
+DRAM_TRAFFIC = {   # (workload, form, queries per step)
+    ("large", "fp16", 2000): dict(exact=63.97e9, approx=23.08e9,
+                                  source="profiles/k_tc_scan_dram_100M_x256_fp16.md"),
 }
 
 SM_COUNT_GB300 = 152
@@ -613,7 +614,7 @@ def main():
         flops = 2.0 * n * agg["tc_pairs"]
         ach = flops / tc_s / 1e12 if tc_s else None
         peak_t = pk.get("bf16_tflops_sustained") or 1713.1
-        dram = DRAM_TRAFFIC.get((args.workload, args.form))
+        dram = DRAM_TRAFFIC.get((args.workload, args.form, B))
         roof = dict(bound="tensor", achieved=ach, peak=peak_t, unit="TFLOP/s", frac=(ach or 0) / peak_t,
                     traffic=dram["exact"] if dram else None, kernel="k_tc_scan",
                     traffic_note=("DRAM bytes per exact-step launch (%s)" % dram["source"]) if dram else None,
