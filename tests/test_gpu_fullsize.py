@@ -48,6 +48,8 @@ SIZES = {
 def test_full_size_sample_matches_oracle(hb, oracle_lib, name):
     N, n, tau, B, sig, ks, form, sample = SIZES[name]
     wl = _wl()
+    gc.collect()                 # indexes and tensors of earlier tests
+    torch.cuda.empty_cache()
     free, total = torch.cuda.mem_get_info()
     need = N * n * 4 * 2.6 if form == "fp16" else N * n * 4 * 2.1
     if free < need:
