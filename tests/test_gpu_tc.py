@@ -122,3 +122,32 @@ def test_fp16_range_checked(hb):
     Q[1, 0] = -1e5
     with pytest.raises(hb.HerculesError):
         idx.query(Q, 3, flags=hb.HK_Q_BF16)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_tc_edge_cases(hb, oracle_lib, fmt):
+    """The precision form at its edges: one series, k = N with leaves of one
+    series up to a single leaf, the shortest series (16 points), a lone
+    query, and batches that cross the 128-row query block."""
+    wl = _wl()
+    bf = hb.HK_BUILD_BF16 if fmt == "bf16" else hb.HK_BUILD_FP16
+    X = wl.random_walk(1, 32, seed=11, device="cuda")
+    idx = hb.Index(X, 10, flags=bf)
+    ids, dist, _ = idx.query(X.clone(), 1, flags=hb.HK_Q_BF16)
+    assert ids.item() == 0 and dist.item() == 0.0
+    X = wl.random_walk(40, 32, seed=12, device="cuda")
+    Q, _ = wl.queries(X, 3, 0.5, seed=13)
+    for tau in (1, 5, 100):
+        idx = hb.Index(X, tau, flags=bf)
+        ids, dist, _ = idx.query(Q, 40, flags=hb.HK_Q_BF16)
+        oids, od2 = oracle.knn(X.cpu().numpy(), Q.cpu().numpy(), 40)
+        np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+        np.testing.assert_allclose(dist.cpu().numpy(), np.sqrt(od2).astype(np.float32), rtol=1e-5)
+    X = wl.random_walk(3000, 16, seed=14, device="cuda")
+    idx = hb.Index(X, 100, flags=bf)
+    for nq in (1, 129, 300):
+        Q, _ = wl.queries(X, nq, [0.2, 1.0], seed=nq)
+        ids, dist, _ = idx.query(Q, 7, flags=hb.HK_Q_BF16)
+        oids, od2 = oracle.knn(X.cpu().numpy(), Q.cpu().numpy(), 7)
+        np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+        np.testing.assert_allclose(dist.cpu().numpy(), np.sqrt(od2).astype(np.float32), rtol=1e-5)
