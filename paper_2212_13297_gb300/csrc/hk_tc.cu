@@ -61,8 +61,11 @@ constexpr int kTcStages = 3;
 constexpr int kTcStageBytes = kTcN * 256 * 2;   // longest series (256 points)
 // Norm slots: tile g uses slot g % 8.  The producer writes tile g's norms
 // after the MMA finished tile g - kTcStages, which it issued after the
-// epilogue released tile g - kTcStages - kAcc: tile g-8 (the slot's previous
-// user) was read before.
+// epilogue released the accumulator of tile g - kTcStages - kAcc.  The
+// epilogue releases a tile's accumulator once it is in registers, before
+// reading that tile's norms, but only after it finished every earlier tile:
+// tile g - kTcStages - kAcc - 1 = g-7 and so g-8 (the slot's previous user)
+// were read before.
 constexpr int kNormSlots = 8;
 constexpr int kTcEpiWarps = 8;   // two per TMEM lane quarter, each half the columns
 constexpr int kTcEpiThreads = 32 * kTcEpiWarps;
@@ -440,6 +443,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                                         (uint32_t)(b * kTcN + (cq * kEpiChunks + h) * 32),
                                     raw[h]);
                 tmem_wait_ld();
+                // the accumulator is in registers: release it to the MMAs
+                // before filtering
+                tc_fence_before();
+                mbar_arrive(&S.acc_empty[b]);
 #pragma unroll
                 for (int h = 0; h < kEpiChunks; ++h) {
                 const int cb = (cq * kEpiChunks + h) * 32;
@@ -517,8 +524,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                     }
                 }
                 }
-                tc_fence_before();
-                mbar_arrive(&S.acc_empty[b]);
                 if (q >= 0 && kth < U) {
                     U = kth;
                     atomicMin(&A.U[q], __float_as_uint(kth));
