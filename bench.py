@@ -40,6 +40,9 @@ WORKLOADS = {
                       desc="2M random walks x 256, leaf 20K, 1000 hard queries (sigma 0.5/1.0), k=10"),
     "tcleaf100k": dict(N=4_000_000, n=256, tau=100_000, nq=1000, sigmas=[0.5, 1.0], k=10, batch=1000,
                        desc="4M random walks x 256, leaf 100K, 1000 hard queries (sigma 0.5/1.0), k=10"),
+    "precprofile": dict(N=2_000_000, n=256, tau=10_000, nq=1024, sigmas=("uniform", 0.01, 1.0), k=100,
+                        batch=1024,
+                        desc="2M random walks x 256, leaf 10K, 1024 queries (sigma uniform in [0.01, 1.0]), k=100"),
     "profile": dict(N=2_000_000, n=256, tau=10_000, nq=200, sigmas=[0.5, 1.0], k=10, batch=200,
                     desc="2M random walks x 256, leaf 10K, 200 hard queries (sigma 0.5/1.0), k=10"),
     "small": dict(N=100_000, n=256, tau=1_000, nq=10, sigmas=[0.1], k=1, batch=10,

@@ -791,7 +791,14 @@ __global__ void k_pool_kth(const float *__restrict__ pool_d, const int32_t *__re
 }
 
 // a8: binary64 rescore of every pooled candidate at or below T(U) and the
-// final top-k by (binary64 distance, original id).
+// final top-k by (binary64 distance, original id).  The candidates at or
+// below T are normally few (about k): their positions are gathered first so
+// that every lane of a warp rescores one (the binary64 pipe is narrow and
+// issues whole warps), then they are sorted in shared memory (bitonic, by
+// (distance, id)).  A larger set takes k block-wide argmin passes over the
+// pool in global memory.
+constexpr int kFinalCap = 1024;
+constexpr int kFinalQLen = 1024;   // longest query held as binary64 in shared memory
 __global__ void k_final(const float *__restrict__ Q, const float *__restrict__ X, int n,
                         const int64_t *__restrict__ perm, const float *__restrict__ pool_d,
                         const int32_t *__restrict__ pool_p, const int32_t *__restrict__ pool_cnt,
@@ -802,26 +809,85 @@ __global__ void k_final(const float *__restrict__ Q, const float *__restrict__ X
     __shared__ double bd[32];
     __shared__ long long bi[32];
     __shared__ int be[32];
+    __shared__ double sv[kFinalCap];
+    __shared__ long long sid[kFinalCap];
+    __shared__ double qd[kFinalQLen];
+    __shared__ int ns;
     const int q = qsel ? qsel[blockIdx.x] : blockIdx.x;
     const int64_t slot = qsel ? blockIdx.x : q;   // row of the pool for this block
     if (qflag && (qflag[q] & 1)) return;
+    if (threadIdx.x == 0) ns = 0;
+    const float *qr = Q + (int64_t)q * n;
+    if (n <= kFinalQLen)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) qd[j] = (double)qr[j];
+    __syncthreads();
     const int cnt = min(pool_cnt[slot], C);
     const float T = __fmul_ru(__uint_as_float(U[q]), 1.0f + rho);
     const float *pd = pool_d + slot * C;
     const int32_t *pp = pool_p + slot * C;
     double *r = rs + slot * C;
-    int resc = 0;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        double v = INFINITY;
+    // the candidates at or below T, positions into sid (as pool indices)
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
         if (pd[i] <= T) {
-            const int64_t pos = pp[i];
-            v = dist2_64(Q + (int64_t)q * n, X + pos * n, n);
-            ++resc;
+            const int e = atomicAdd(&ns, 1);
+            if (e < kFinalCap) sid[e] = i;
         }
-        r[i] = v;
+    __syncthreads();
+    const int m = ns;
+    if (threadIdx.x == 0 && m) stat_add(&stats[ST_RESCORED], m);
+    if (m <= kFinalCap) {
+        for (int e = threadIdx.x; e < m; e += blockDim.x) {
+            const int64_t pos = pp[sid[e]];
+            const float *x = X + pos * n;
+            double v = 0.0;   // dist2_64, with the query's binary64 values from shared memory
+            if (n <= kFinalQLen) {
+                for (int j = 0; j < n; ++j) {
+                    const double d = __dsub_rn(qd[j], (double)x[j]);
+                    v = __dadd_rn(v, __dmul_rn(d, d));
+                }
+            } else {
+                v = dist2_64(qr, x, n);
+            }
+            sv[e] = v;
+            sid[e] = perm ? perm[pos] : pos;
+        }
+        int P = 1;
+        while (P < m) P <<= 1;
+        for (int i = m + threadIdx.x; i < P; i += blockDim.x) {
+            sv[i] = INFINITY;
+            sid[i] = 0x7fffffffffffffffLL;
+        }
+        __syncthreads();
+        for (int size = 2; size <= P; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                    const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+                    const bool gt = sv[i] > sv[j] || (sv[i] == sv[j] && sid[i] > sid[j]);
+                    if (gt == ((i & size) == 0)) {
+                        const double tv = sv[i];
+                        sv[i] = sv[j];
+                        sv[j] = tv;
+                        const long long ti = sid[i];
+                        sid[i] = sid[j];
+                        sid[j] = ti;
+                    }
+                }
+                __syncthreads();
+            }
+        for (int t = threadIdx.x; t < k; t += blockDim.x) {
+            if (t < m) {
+                out_ids[(int64_t)q * k + t] = sid[t];
+                out_dist[(int64_t)q * k + t] = __double2float_rn(__dsqrt_rn(sv[t]));
+            } else {
+                atomicOr(err, 1);
+                out_ids[(int64_t)q * k + t] = -1;
+                out_dist[(int64_t)q * k + t] = INFINITY;
+            }
+        }
+        return;
     }
-    resc = warp_sum_i(resc);
-    if ((threadIdx.x & 31) == 0 && resc) stat_add(&stats[ST_RESCORED], resc);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
+        r[i] = pd[i] <= T ? dist2_64(qr, X + (int64_t)pp[i] * n, n) : INFINITY;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = 0; t < k; ++t) {

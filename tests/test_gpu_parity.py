@@ -228,6 +228,22 @@ def test_edge_cases(hb, oracle_lib):
     assert ids.cpu().tolist() == [[0, 1, 2, 3]]
 
 
+def test_largest_k_and_many_candidates_at_the_bound(hb, oracle_lib):
+    """k = HK_MAX_K = 1024.  One query equals a row copied 2,000 times, so
+    more than 1,024 candidates sit at the final bound (the selection over the
+    pool in global memory); the others leave about k (the shared-memory
+    sort).  Plain and precision forms."""
+    wl = _wl()
+    X = wl.random_walk(6000, 64, seed=21, device="cuda")
+    X[1000:3000] = X[17]
+    Q = torch.cat([X[[17]], wl.queries(X, 3, [0.3, 1.0], seed=22)[0]]).contiguous()
+    for qflags, bflags in ((0, 0), (hb.HK_Q_BF16, hb.HK_BUILD_FP16)):
+        idx = hb.Index(X, 200, flags=bflags)
+        ids, dist, _ = idx.query(Q, 1024, flags=qflags)
+        check_answers(ids, dist, X.cpu().numpy(), Q.cpu().numpy(), 1024)
+        assert ids[0].cpu().tolist() == [17] + list(range(1000, 2023))
+
+
 def test_rejects_nonfinite_and_bad_k(hb):
     wl = _wl()
     X = wl.random_walk(100, 32, seed=1, device="cuda")
