@@ -122,6 +122,8 @@ struct Workspace {
     DevBuf<float> q2, qa, qoff; // query |q|^2 (1-eb) - abs term, error coefficient, 2 x abs term
     DevBuf<int> bad;            // a query outside the 16-bit format's range
     DevBuf<int32_t> cand_cnt;   // nq    tensor-core candidates per query
+    DevBuf<int32_t> rs_items;   // nq    rescore work items per query
+    DevBuf<int32_t> rs_off;     // nq + 1  their exclusive scan
     DevBuf<int32_t> cand_p;     // nq * cand_C
     DevBuf<float> cand_lb;      // nq * cand_C  lower bound D~ - E
     DevBuf<uint32_t> Uinit;     // retry pass: starting bounds
@@ -281,7 +283,8 @@ void launch_tc_qprep(const float *Q, int nq, int n, int fmt, double xn_max, void
 void launch_tc_rescore(const float *Q, const float *X, int n, int nq, const int32_t *cand_cnt,
                        const int32_t *cand_p, const float *cand_lb, int cand_C, const uint32_t *U,
                        float *pool_d, int32_t *pool_p, int32_t *pool_cnt, int pool_C, int32_t *qflag,
-                       long long *stats, int stat_slot, cudaStream_t s);
+                       long long *stats, int stat_slot, int32_t *items, int32_t *item_off,
+                       DevBuf<int32_t> &scan_tmp, cudaStream_t s);
 size_t tc_smem_bytes(int n);
 void launch_max_norm(const void *xq, int64_t N, unsigned *out, cudaStream_t s);
 uint32_t tc_idesc(int fmt);
@@ -292,7 +295,10 @@ constexpr int kTcLocalK = 16;     // largest k whose best upper bounds the tenso
 // Candidate-list and pool length per query in the precision form: its
 // certified band admits the near neighbours around the k-th distance, more
 // of them as k grows (an overflow reruns the query on the float32 path).
-inline int tc_list_cap(int k) { return k * 1024 > 65536 ? k * 1024 : 65536; }
+inline int tc_list_cap(int k) {
+    const int c = k * 4096 < (1 << 20) ? k * 4096 : (1 << 20);
+    return c > 65536 ? c : 65536;
+}
 
 // Exhaustive exact k-NN into caller device buffers using only `sc`.
 void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq, int k,

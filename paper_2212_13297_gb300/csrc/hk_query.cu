@@ -767,27 +767,59 @@ __global__ void k_stats_init(long long *__restrict__ stats, int nq, long long L)
     }
 }
 
+// U[q] from the k-th smallest pooled distance (rounded up by T's factor):
+// a radix select over the distances' bit patterns (non-negative floats order
+// as their bits), four passes of 8 bits with a shared-memory histogram.
 __global__ void k_pool_kth(const float *__restrict__ pool_d, const int32_t *__restrict__ pool_cnt,
                            int C, int k, float rho, uint32_t *__restrict__ U) {
-    __shared__ int red[32];
+    __shared__ int hist[257];
+    __shared__ uint32_t s_prefix;
+    __shared__ int s_rank;
     const int q = blockIdx.x;
     const int cnt = min(pool_cnt[q], C);
     if (cnt < k) return;
-    const float *d = pool_d + (int64_t)q * C;
-    uint32_t lo = 0, hi = 0x7f800000u;
-    while (lo < hi) {
-        const uint32_t mid = lo + ((hi - lo) >> 1);
-        int c = 0;
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) c += __float_as_uint(d[i]) <= mid;
-        c = warp_sum_i(c);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    const uint32_t *d = reinterpret_cast<const uint32_t *>(pool_d + (int64_t)q * C);
+    const int lane = threadIdx.x & 31;
+    uint32_t prefix = 0, mask = 0;
+    int rank = k;   // rank of the wanted key among those matching the prefix
+    // keys are read kKthUnroll per thread at a time, so that a large pool's
+    // pass is not a chain of single dependent loads
+    constexpr int kKthUnroll = 8;
+    const int span = blockDim.x * kKthUnroll;
+    const int rounds = (cnt + span - 1) / span;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
         __syncthreads();
-        int tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        for (int r = 0; r < rounds; ++r) {
+            uint32_t key[kKthUnroll];
+#pragma unroll
+            for (int u = 0; u < kKthUnroll; ++u) {
+                const int i = r * span + u * blockDim.x + threadIdx.x;
+                key[u] = i < cnt ? d[i] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < kKthUnroll; ++u) {
+                const int i = r * span + u * blockDim.x + threadIdx.x;
+                int digit = 256;   // no count
+                if (i < cnt && (key[u] & mask) == prefix) digit = (int)((key[u] >> shift) & 255u);
+                const unsigned peers = __match_any_sync(0xffffffffu, digit);
+                if (digit < 256 && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], __popc(peers));
+            }
+        }
         __syncthreads();
-        if (tot >= k) hi = mid; else lo = mid + 1;
+        if (threadIdx.x == 0) {
+            int cum = 0, b = 0;
+            for (; b < 255 && cum + hist[b] < rank; ++b) cum += hist[b];
+            s_prefix = prefix | ((uint32_t)b << shift);
+            s_rank = rank - cum;
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        rank = s_rank;
+        mask |= 255u << shift;
+        __syncthreads();
     }
-    if (threadIdx.x == 0) atomicMin(&U[q], __float_as_uint(upper_f(__uint_as_float(lo), rho)));
+    if (threadIdx.x == 0) atomicMin(&U[q], __float_as_uint(upper_f(__uint_as_float(prefix), rho)));
 }
 
 // a8: binary64 rescore of every pooled candidate at or below T(U) and the
@@ -826,12 +858,24 @@ __global__ void k_final(const float *__restrict__ Q, const float *__restrict__ X
     const float *pd = pool_d + slot * C;
     const int32_t *pp = pool_p + slot * C;
     double *r = rs + slot * C;
-    // the candidates at or below T, positions into sid (as pool indices)
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
-        if (pd[i] <= T) {
-            const int e = atomicAdd(&ns, 1);
-            if (e < kFinalCap) sid[e] = i;
+    // the candidates at or below T, positions into sid (as pool indices);
+    // eight loads in flight per thread
+    for (int i0 = 0; i0 < cnt; i0 += 8 * blockDim.x) {
+        float dv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * blockDim.x + threadIdx.x;
+            dv[u] = i < cnt ? pd[i] : INFINITY;
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * blockDim.x + threadIdx.x;
+            if (i < cnt && dv[u] <= T) {
+                const int e = atomicAdd(&ns, 1);
+                if (e < kFinalCap) sid[e] = i;
+            }
+        }
+    }
     __syncthreads();
     const int m = ns;
     if (threadIdx.x == 0 && m) stat_add(&stats[ST_RESCORED], m);
@@ -1138,6 +1182,8 @@ void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, 
     const int n = idx->n;
     const int cand_C = tc_list_cap(k);
     ws.cand_cnt.reserve(nq, s);
+    ws.rs_items.reserve(nq, s);
+    ws.rs_off.reserve((size_t)nq + 1, s);
     ws.cand_p.reserve((size_t)nq * cand_C, s);
     ws.cand_lb.reserve((size_t)nq * cand_C, s);
     HK_CHECK_CUDA(cudaMemsetAsync(ws.cand_cnt.p, 0, nq * sizeof(int32_t), s));
@@ -1181,7 +1227,7 @@ void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, 
     HK_CHECK_LAUNCH();
     launch_tc_rescore(Qd, v.X, n, nq, ws.cand_cnt.p, ws.cand_p.p, ws.cand_lb.p, cand_C, ws.U.p,
                       ws.pool_d.p, ws.pool_p.p, ws.pool_cnt.p, pool_C, ws.qflag.p,
-                      (long long *)ws.stats.p, ST_FULL, s);
+                      (long long *)ws.stats.p, ST_FULL, ws.rs_items.p, ws.rs_off.p, ws.scan_tmp32, s);
     if (capture) return;
     int32_t terr = 0;
     HK_CHECK_CUDA(cudaMemcpyAsync(&terr, ws.counters.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

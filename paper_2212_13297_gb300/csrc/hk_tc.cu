@@ -637,76 +637,94 @@ __global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, int fmt, 
 }
 
 // Exact float32 distances of the candidates at or below the final bound into
-// the query's pool: a warp per candidate, 16-byte loads of the row, the query
-// in shared memory.  Any summation order stays within the rounding bound that
-// T(U) allows for.
-__global__ void k_tc_rescore(const float *__restrict__ Q, const float *__restrict__ X, int n,
+// the query's pool.  Work items are runs of kRescoreChunk candidates of one
+// query (item_off: exclusive scan of the items per query), spread over a
+// persistent grid so that a query with many candidates does not hold up the
+// launch.  A warp reads 32 candidates' bounds and positions at once, then
+// rescores the live ones two rows at a time with 16-byte loads.  Any
+// summation order stays within the rounding bound that T(U) allows for.
+constexpr int kRescoreChunk = 256;
+__global__ void k_rescore_items(const int32_t *__restrict__ cand_cnt, int nq, int cand_C,
+                                int32_t *__restrict__ items) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x)
+        items[q] = (min(cand_cnt[q], cand_C) + kRescoreChunk - 1) / kRescoreChunk;
+}
+
+__global__ void k_tc_rescore(const float *__restrict__ Q, const float *__restrict__ X, int n, int nq,
+                             const int32_t *__restrict__ item_off,
                              const int32_t *__restrict__ cand_cnt, const int32_t *__restrict__ cand_p,
                              const float *__restrict__ cand_lb, int cand_C,
                              const uint32_t *__restrict__ U, float *__restrict__ pool_d,
                              int32_t *__restrict__ pool_p, int32_t *__restrict__ pool_cnt, int pool_C,
                              int32_t *__restrict__ qflag, long long *__restrict__ stats, int stat_slot) {
-    extern __shared__ float4 q4s[];   // n / 4
-    const int q = blockIdx.y;
     const int lane = threadIdx.x & 31;
-    const int cnt = min(cand_cnt[q], cand_C);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int total = item_off[nq];
     const int n4 = n / 4;
-    const float4 *q4 = reinterpret_cast<const float4 *>(Q + (int64_t)q * n);
-    for (int j = threadIdx.x; j < n4; j += blockDim.x) q4s[j] = q4[j];
-    __syncthreads();
-    const float u = __uint_as_float(U[q]);
-    const int wpb = blockDim.x >> 5;
     long long done = 0;
-    // a warp reads 32 candidates' bounds and positions at once, then rescores
-    // the live ones two rows at a time
-    for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; c0 < cnt; c0 += gridDim.x * wpb * 32) {
-        const int c = c0 + lane;
-        float lb = INFINITY;
-        int32_t pos = 0;
-        if (c < cnt) {
-            lb = cand_lb[(int64_t)q * cand_C + c];
-            pos = cand_p[(int64_t)q * cand_C + c];
+    for (int64_t it = gw; it < total; it += nw) {
+        // the item's query: the last q with item_off[q] <= it
+        int lo = 0, hi = nq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_off[mid] <= it) lo = mid; else hi = mid - 1;
         }
-        unsigned live = __ballot_sync(0xffffffffu, lb <= u);
-        while (live) {
-            const int i1 = __ffs(live) - 1;
-            live &= live - 1;
-            const int i2 = live ? __ffs(live) - 1 : i1;
-            if (live) live &= live - 1;
-            const int32_t p1 = __shfl_sync(0xffffffffu, pos, i1);
-            const int32_t p2 = __shfl_sync(0xffffffffu, pos, i2);
-            const float4 *x1 = reinterpret_cast<const float4 *>(X + (int64_t)p1 * n);
-            const float4 *x2 = reinterpret_cast<const float4 *>(X + (int64_t)p2 * n);
-            float a1 = 0.0f, a2 = 0.0f;
-            for (int j = lane; j < n4; j += 32) {
-                const float4 u1 = x1[j], u2 = x2[j], qv = q4s[j];
-                float d;
-                d = qv.x - u1.x; a1 = fmaf(d, d, a1);
-                d = qv.y - u1.y; a1 = fmaf(d, d, a1);
-                d = qv.z - u1.z; a1 = fmaf(d, d, a1);
-                d = qv.w - u1.w; a1 = fmaf(d, d, a1);
-                d = qv.x - u2.x; a2 = fmaf(d, d, a2);
-                d = qv.y - u2.y; a2 = fmaf(d, d, a2);
-                d = qv.z - u2.z; a2 = fmaf(d, d, a2);
-                d = qv.w - u2.w; a2 = fmaf(d, d, a2);
+        const int q = lo;
+        const int cnt = min(cand_cnt[q], cand_C);
+        const int cb = (int)(it - item_off[q]) * kRescoreChunk;
+        const int ce = min(cb + kRescoreChunk, cnt);
+        const float u = __uint_as_float(U[q]);
+        const float4 *q4 = reinterpret_cast<const float4 *>(Q + (int64_t)q * n);
+        for (int c0 = cb; c0 < ce; c0 += 32) {
+            const int c = c0 + lane;
+            float lb = INFINITY;
+            int32_t pos = 0;
+            if (c < ce) {
+                lb = cand_lb[(int64_t)q * cand_C + c];
+                pos = cand_p[(int64_t)q * cand_C + c];
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-            }
-            if (lane == 0) {
-                const int m = i2 != i1 ? 2 : 1;
-                done += m;
-                const int slot = atomicAdd(&pool_cnt[q], m);
-                if (slot < pool_C) {
-                    pool_d[(int64_t)q * pool_C + slot] = a1;
-                    pool_p[(int64_t)q * pool_C + slot] = p1;
+            unsigned live = __ballot_sync(0xffffffffu, lb <= u);
+            while (live) {
+                const int i1 = __ffs(live) - 1;
+                live &= live - 1;
+                const int i2 = live ? __ffs(live) - 1 : i1;
+                if (live) live &= live - 1;
+                const int32_t p1 = __shfl_sync(0xffffffffu, pos, i1);
+                const int32_t p2 = __shfl_sync(0xffffffffu, pos, i2);
+                const float4 *x1 = reinterpret_cast<const float4 *>(X + (int64_t)p1 * n);
+                const float4 *x2 = reinterpret_cast<const float4 *>(X + (int64_t)p2 * n);
+                float a1 = 0.0f, a2 = 0.0f;
+                for (int j = lane; j < n4; j += 32) {
+                    const float4 u1 = x1[j], u2 = x2[j], qv = q4[j];
+                    float d;
+                    d = qv.x - u1.x; a1 = fmaf(d, d, a1);
+                    d = qv.y - u1.y; a1 = fmaf(d, d, a1);
+                    d = qv.z - u1.z; a1 = fmaf(d, d, a1);
+                    d = qv.w - u1.w; a1 = fmaf(d, d, a1);
+                    d = qv.x - u2.x; a2 = fmaf(d, d, a2);
+                    d = qv.y - u2.y; a2 = fmaf(d, d, a2);
+                    d = qv.z - u2.z; a2 = fmaf(d, d, a2);
+                    d = qv.w - u2.w; a2 = fmaf(d, d, a2);
                 }
-                if (m == 2 && slot + 1 < pool_C) {
-                    pool_d[(int64_t)q * pool_C + slot + 1] = a2;
-                    pool_p[(int64_t)q * pool_C + slot + 1] = p2;
+                for (int o = 16; o > 0; o >>= 1) {
+                    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
                 }
-                if (slot + m > pool_C) atomicOr(&qflag[q], 1);
+                if (lane == 0) {
+                    const int m = i2 != i1 ? 2 : 1;
+                    done += m;
+                    const int slot = atomicAdd(&pool_cnt[q], m);
+                    if (slot < pool_C) {
+                        pool_d[(int64_t)q * pool_C + slot] = a1;
+                        pool_p[(int64_t)q * pool_C + slot] = p1;
+                    }
+                    if (m == 2 && slot + 1 < pool_C) {
+                        pool_d[(int64_t)q * pool_C + slot + 1] = a2;
+                        pool_p[(int64_t)q * pool_C + slot + 1] = p2;
+                    }
+                    if (slot + m > pool_C) atomicOr(&qflag[q], 1);
+                }
             }
         }
     }
@@ -792,10 +810,16 @@ void launch_max_norm(const void *xq, int64_t N, unsigned *out, cudaStream_t s) {
 void launch_tc_rescore(const float *Q, const float *X, int n, int nq, const int32_t *cand_cnt,
                        const int32_t *cand_p, const float *cand_lb, int cand_C, const uint32_t *U,
                        float *pool_d, int32_t *pool_p, int32_t *pool_cnt, int pool_C, int32_t *qflag,
-                       long long *stats, int stat_slot, cudaStream_t s) {
-    dim3 grid(8, (unsigned)nq);
-    k_tc_rescore<<<grid, 256, (size_t)n * sizeof(float), s>>>(Q, X, n, cand_cnt, cand_p, cand_lb, cand_C, U, pool_d, pool_p,
-                                      pool_cnt, pool_C, qflag, stats, stat_slot);
+                       long long *stats, int stat_slot, int32_t *items, int32_t *item_off,
+                       DevBuf<int32_t> &scan_tmp, cudaStream_t s) {
+    k_rescore_items<<<(nq + 255) / 256, 256, 0, s>>>(cand_cnt, nq, cand_C, items);
+    HK_CHECK_LAUNCH();
+    exclusive_scan_i32(items, item_off, nq, s, scan_tmp);
+    int dev = 0, sms = 0;
+    HK_CHECK_CUDA(cudaGetDevice(&dev));
+    HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    k_tc_rescore<<<sms * 8, 256, 0, s>>>(Q, X, n, nq, item_off, cand_cnt, cand_p, cand_lb, cand_C, U,
+                                         pool_d, pool_p, pool_cnt, pool_C, qflag, stats, stat_slot);
     HK_CHECK_LAUNCH();
 }
 
