@@ -1223,7 +1223,7 @@ void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, 
     if (tctimer) tctimer->mark(s);
     launch_tc_scan(t, s);
     if (tctimer) tctimer->mark(s);
-    k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+    k_pool_kth<<<nq, 512, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
     HK_CHECK_LAUNCH();
     launch_tc_rescore(Qd, v.X, n, nq, ws.cand_cnt.p, ws.cand_p.p, ws.cand_lb.p, cand_C, ws.U.p,
                       ws.pool_d.p, ws.pool_p.p, ws.pool_cnt.p, pool_C, ws.qflag.p,
@@ -1273,7 +1273,7 @@ void copy_out(const Workspace &ws, int nq, int k, int64_t *ids, float *dist, cud
 void final_select(Workspace &ws, const LeafView &v, const float *Qd, int nq, int k, int pool_C,
                   float rho, cudaStream_t s, std::vector<int32_t> &flags, std::vector<uint32_t> &U,
                   bool capture = false) {
-    k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+    k_pool_kth<<<nq, 512, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
     HK_CHECK_LAUNCH();
     HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p + 1, 0, sizeof(int32_t), s));
     k_final<<<nq, 256, 0, s>>>(Qd, v.X, v.n, v.perm, ws.pool_d.p, ws.pool_p.p, ws.pool_cnt.p, pool_C,
@@ -1531,7 +1531,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
                                                    (long long *)ws.stats.p, -1, ST_LEAVES_APPROX);
         HK_CHECK_LAUNCH();
-        k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+        k_pool_kth<<<nq, 512, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
         HK_CHECK_LAUNCH();
         HK_CHECK_CUDA(cudaMemsetAsync(ws.qcand.p, 0, nq * sizeof(int32_t), s));
     }
@@ -1562,7 +1562,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
             k_count_items_and_series<<<8, 256, 0, s>>>(ws.item_off.p, L, ws.leaf_qcnt.p, idx->leaf_off.p,
                                                        (long long *)ws.stats.p, ST_SERIES_CAND, -1);
             HK_CHECK_LAUNCH();
-            k_pool_kth<<<nq, 256, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
+            k_pool_kth<<<nq, 512, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
             HK_CHECK_LAUNCH();
             const int64_t pairs = L * (int64_t)nq;
             k_reprune<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(ws.lb.p, L, nq, ws.U.p, ws.mask.p,
@@ -1890,7 +1890,7 @@ void scan_knn_scratch(const float *Xd, int64_t N, int n, const float *Qd, int nq
     a.stats = sc.stats;
     a.use_sax = 0;
     launch_scan(a, cfg, s);
-    k_pool_kth<<<nq, 256, 0, s>>>(sc.pool_d, sc.pool_cnt, sc.pool_C, k, rho, sc.U);
+    k_pool_kth<<<nq, 512, 0, s>>>(sc.pool_d, sc.pool_cnt, sc.pool_C, k, rho, sc.U);
     HK_CHECK_LAUNCH();
     k_final<<<nq, 256, 0, s>>>(Qd, Xd, n, nullptr, sc.pool_d, sc.pool_p, sc.pool_cnt, sc.pool_C, sc.U,
                                sc.qflag, k, rho, sc.rs_d, ids_dev, dist_dev, sc.stats, sc.counters + 1,

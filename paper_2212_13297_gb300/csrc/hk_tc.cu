@@ -641,7 +641,7 @@ __global__ void k_tc_qprep(const float *__restrict__ Q, int nq, int n, int fmt, 
 // query (item_off: exclusive scan of the items per query), spread over a
 // persistent grid so that a query with many candidates does not hold up the
 // launch.  A warp reads 32 candidates' bounds and positions at once, then
-// rescores the live ones two rows at a time with 16-byte loads.  Any
+// rescores the live ones four rows at a time with 16-byte loads.  Any
 // summation order stays within the rounding bound that T(U) allows for.
 constexpr int kRescoreChunk = 256;
 __global__ void k_rescore_items(const int32_t *__restrict__ cand_cnt, int nq, int cand_C,
@@ -686,43 +686,53 @@ __global__ void k_tc_rescore(const float *__restrict__ Q, const float *__restric
             }
             unsigned live = __ballot_sync(0xffffffffu, lb <= u);
             while (live) {
-                const int i1 = __ffs(live) - 1;
-                live &= live - 1;
-                const int i2 = live ? __ffs(live) - 1 : i1;
-                if (live) live &= live - 1;
-                const int32_t p1 = __shfl_sync(0xffffffffu, pos, i1);
-                const int32_t p2 = __shfl_sync(0xffffffffu, pos, i2);
-                const float4 *x1 = reinterpret_cast<const float4 *>(X + (int64_t)p1 * n);
-                const float4 *x2 = reinterpret_cast<const float4 *>(X + (int64_t)p2 * n);
-                float a1 = 0.0f, a2 = 0.0f;
+                // up to four live candidates at once (repeats of the last
+                // one fill the slots and are not stored)
+                int ii[4];
+                int m = 0;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (live) {
+                        ii[r] = __ffs(live) - 1;
+                        live &= live - 1;
+                        m = r + 1;
+                    } else {
+                        ii[r] = ii[r > 0 ? r - 1 : 0];
+                    }
+                }
+                int32_t pr[4];
+                const float4 *xr[4];
+                float a[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    pr[r] = __shfl_sync(0xffffffffu, pos, ii[r]);
+                    xr[r] = reinterpret_cast<const float4 *>(X + (int64_t)pr[r] * n);
+                    a[r] = 0.0f;
+                }
                 for (int j = lane; j < n4; j += 32) {
-                    const float4 u1 = x1[j], u2 = x2[j], qv = q4[j];
-                    float d;
-                    d = qv.x - u1.x; a1 = fmaf(d, d, a1);
-                    d = qv.y - u1.y; a1 = fmaf(d, d, a1);
-                    d = qv.z - u1.z; a1 = fmaf(d, d, a1);
-                    d = qv.w - u1.w; a1 = fmaf(d, d, a1);
-                    d = qv.x - u2.x; a2 = fmaf(d, d, a2);
-                    d = qv.y - u2.y; a2 = fmaf(d, d, a2);
-                    d = qv.z - u2.z; a2 = fmaf(d, d, a2);
-                    d = qv.w - u2.w; a2 = fmaf(d, d, a2);
+                    const float4 qv = q4[j];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float4 xv = xr[r][j];
+                        float d;
+                        d = qv.x - xv.x; a[r] = fmaf(d, d, a[r]);
+                        d = qv.y - xv.y; a[r] = fmaf(d, d, a[r]);
+                        d = qv.z - xv.z; a[r] = fmaf(d, d, a[r]);
+                        d = qv.w - xv.w; a[r] = fmaf(d, d, a[r]);
+                    }
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    for (int o = 16; o > 0; o >>= 1) a[r] += __shfl_xor_sync(0xffffffffu, a[r], o);
                 if (lane == 0) {
-                    const int m = i2 != i1 ? 2 : 1;
                     done += m;
                     const int slot = atomicAdd(&pool_cnt[q], m);
-                    if (slot < pool_C) {
-                        pool_d[(int64_t)q * pool_C + slot] = a1;
-                        pool_p[(int64_t)q * pool_C + slot] = p1;
-                    }
-                    if (m == 2 && slot + 1 < pool_C) {
-                        pool_d[(int64_t)q * pool_C + slot + 1] = a2;
-                        pool_p[(int64_t)q * pool_C + slot + 1] = p2;
-                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (r < m && slot + r < pool_C) {
+                            pool_d[(int64_t)q * pool_C + slot + r] = a[r];
+                            pool_p[(int64_t)q * pool_C + slot + r] = pr[r];
+                        }
                     if (slot + m > pool_C) atomicOr(&qflag[q], 1);
                 }
             }
