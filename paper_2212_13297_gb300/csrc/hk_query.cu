@@ -772,7 +772,7 @@ __global__ void k_stats_init(long long *__restrict__ stats, int nq, long long L)
 // as their bits), four passes of 8 bits with a shared-memory histogram.
 __global__ void k_pool_kth(const float *__restrict__ pool_d, const int32_t *__restrict__ pool_cnt,
                            int C, int k, float rho, uint32_t *__restrict__ U) {
-    __shared__ int hist[257];
+    __shared__ int hist[256];
     __shared__ uint32_t s_prefix;
     __shared__ int s_rank;
     const int q = blockIdx.x;
