@@ -427,6 +427,64 @@ def ablation(args):
                           config=dict(workload=wl["desc"]), data="synthetic", variants=out)), flush=True)
 
 
+def tune_graph(args):
+    """Form (2) measured: hk_tune's choice against the library's defaults, and
+    CUDA-graph replay (HK_Q_GRAPH) against ordinary calls, on a 10M x 256
+    random-walk collection (leaf 10K, float16 copy), queries of mixed
+    difficulty (sigma 0.01 / 0.1 / 0.5 / 1.0), k = 10.  The tuner sees one
+    batch; the configurations are timed on the next.  Prints one JSON line."""
+    import torch
+    from paper_2212_13297_gb300 import binding, workload
+    import __graft_entry__
+    __graft_entry__.build()
+    N, n, tau, k = 10_000_000, 256, 10_000, 10
+    X = workload.random_walk(N, n, seed=0, device="cuda")
+    Qall, _ = workload.queries(X, 4096, [0.01, 0.1, 0.5, 1.0], seed=1)
+    idx = binding.Index(X, tau, flags=binding.HK_BUILD_FP16)
+    del X
+    torch.cuda.empty_cache()
+
+    def ms_per_call(Q, kw, reps):
+        ids = torch.empty((Q.shape[0], k), dtype=torch.int64, device="cuda")
+        dist = torch.empty((Q.shape[0], k), dtype=torch.float32, device="cuda")
+        for _ in range(max(3, args.warmup)):
+            idx.query(Q, k, out=(ids, dist), **kw)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(reps):
+            idx.query(Q, k, out=(ids, dist), **kw)
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    tune_rows = []
+    for batch in (64, 512):
+        sample, Q = Qall[:batch].contiguous(), Qall[batch:2 * batch].contiguous()
+        t0 = time.perf_counter()
+        tuned = idx.tune(sample, k)
+        tune_s = time.perf_counter() - t0
+        kw = {key: tuned[key] for key in ("l_max", "eapca_th", "sax_th", "flags", "query_group", "series_tile")}
+        row = dict(batch=batch, tune_s=tune_s, tried=tuned["tried"], chosen=dict(kw, tensor_cores=tuned["tensor_cores"]))
+        for name, qkw in (("default_float32", dict(flags=0)), ("default_precision", dict(flags=binding.HK_Q_BF16)),
+                          ("tuned", kw)):
+            ms = ms_per_call(Q, qkw, 5)
+            row[name] = dict(ms_per_batch=ms, queries_per_s=batch / ms * 1e3)
+        tune_rows.append(row)
+    graph_rows = []
+    for batch in (1, 8, 64, 512):
+        Q = Qall[:batch].contiguous()
+        plain = ms_per_call(Q, dict(flags=binding.HK_Q_BF16), 20)
+        graph = ms_per_call(Q, dict(flags=binding.HK_Q_BF16 | binding.HK_Q_GRAPH), 20)
+        graph_rows.append(dict(batch=batch, ms_per_batch_launches=plain, ms_per_batch_graph=graph,
+                               speedup=plain / graph))
+    print(json.dumps(dict(metric="form (2): autotuned configuration and CUDA-graph replay, exact 10-NN",
+                          unit="ms per batch", data="synthetic",
+                          config=dict(workload="10M random walks x 256, leaf 10K, float16 copy, "
+                                               "sigma 0.01/0.1/0.5/1.0, k=10"),
+                          autotune=tune_rows, graphs=graph_rows)), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,6 +510,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--ablation", action="store_true",
                     help="instead of the step benchmark, the NoSAX / NoThresh ablation on the mid workload")
+    ap.add_argument("--tune-graph", action="store_true",
+                    help="instead of the step benchmark, hk_tune's choice against the defaults and "
+                         "CUDA-graph replay against ordinary calls (10M x 256)")
     ap.add_argument("--serve-mix", type=float, default=0.0,
                     help="instead of the step benchmark, serve the four-collection mix at this "
                          "rate (requests/s) and print its latency line")
@@ -468,6 +529,9 @@ def main():
         return
     if args.ablation:
         ablation(args)
+        return
+    if args.tune_graph:
+        tune_graph(args)
         return
 
     import numpy as np
