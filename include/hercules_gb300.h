@@ -188,6 +188,9 @@ typedef struct {
  * Row i lists query i's neighbours ascending by (binary64 squared distance
  * summed in index order, id): the brute-force answer, ties to the lower id.
  * stats may be NULL; opts may be NULL (defaults).
+ * Calls on one index share its work space (and its staging buffer for host
+ * queries): they must not run concurrently; the server (hk_server_*) answers
+ * concurrent requests.
  */
 int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k,
              const hk_query_opts *opts, void *stream, int64_t *out_ids,

@@ -145,8 +145,15 @@ int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k, const hk_quer
         }
         cudaStream_t s = (cudaStream_t)stream;
         idx->stream = s;
-        hk::DevBuf<float> tmp;
-        const float *Qd = device_view(Q, (size_t)nq * idx->n, s, tmp);
+        // host queries go through the index's staging buffer: no device
+        // allocation (and no cudaFree, which waits for the device) per call
+        const float *Qd = Q;
+        if (!hk::is_device_ptr(Q)) {
+            const size_t count = (size_t)nq * idx->n;
+            idx->qstage.reserve(count, s);
+            HK_CHECK_CUDA(cudaMemcpyAsync(idx->qstage.p, Q, count * sizeof(float), cudaMemcpyHostToDevice, s));
+            Qd = idx->qstage.p;
+        }
         hk::check_finite(Qd, (int64_t)nq * idx->n, s, "Q");
         hk::run_query(idx, Qd, nq, k, o, s, out_ids, out_dist, stats);
     });

@@ -190,6 +190,7 @@ struct hk_index {
     bool has_bf16 = false;         // a 16-bit copy exists (format fmt16)
     int fmt16 = 1;                 // kFmtBF16 or kFmtF16
     double xn_max = 0.0;           // largest |x| (rounded up)
+    hk::DevBuf<float> qstage;      // device copy of host queries (grows, kept between calls)
 
     std::vector<int64_t> h_leaf_off;
     std::vector<int32_t> h_leaf_nseg;
