@@ -431,7 +431,6 @@ __global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
     __shared__ int s_stage[G], s_list[G];
     __shared__ int64_t s_s0, s_s1;
     __shared__ int s_gq, s_leaf;
-    __shared__ long long s_cnt[4];   // sax pruned, abandoned, full, points
     __shared__ float s_B[kAlpha + 1];          // cell ends: -inf, breakpoints, +inf
     __shared__ float s_paa[G][2 * kWord];      // per query: PAA rounded down, then up
     __shared__ float4 s_pp[(G + 1) / 2][kWord]; // per query pair: (down g, down g+1, up g, up g+1)
@@ -1328,16 +1327,6 @@ void exhaustive_one(Workspace &ws, const LeafView &v, const float *Qd, int q, ui
     HK_CHECK_CUDA(cudaMemcpyAsync(&err, ws.counters.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HK_CHECK_CUDA(cudaStreamSynchronize(s));
     if (err) fail(HK_EINTERNAL, "exhaustive collection for query %d: selection failed", q);
-}
-
-void add_host_stat(Workspace &ws, int slot, long long v, cudaStream_t s) {
-    std::vector<long long> st(kStatSlots);
-    HK_CHECK_CUDA(cudaMemcpyAsync(st.data(), ws.stats.p, kStatSlots * sizeof(long long),
-                                  cudaMemcpyDeviceToHost, s));
-    HK_CHECK_CUDA(cudaStreamSynchronize(s));
-    st[slot] += v;
-    HK_CHECK_CUDA(cudaMemcpyAsync(ws.stats.p, st.data(), kStatSlots * sizeof(long long),
-                                  cudaMemcpyHostToDevice, s));
 }
 
 void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s, ScanTimer *timer,
