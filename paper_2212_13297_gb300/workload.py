@@ -96,6 +96,31 @@ def queries(X: torch.Tensor, nq: int, sigmas, seed: int = 1, norm="z"):
     return q.float().contiguous(), src
 
 
+# The served mix: four device-resident collections (name, N, n, kind, leaf
+# capacity), standing in for the paper's Deep (n = 96, embeddings), SALD
+# (n = 128) and Synth / Seismic (random walks) collections.  Collection i
+# uses data seed 10 + i and query seed 20 + i.
+SERVED_MIX = [
+    ("20M x 96 Gaussian, L2-normalised", 20_000_000, 96, "gauss_l2", 10_000),
+    ("10M x 128 Gaussian", 10_000_000, 128, "gauss", 10_000),
+    ("10M x 256 random walk", 10_000_000, 256, "rw", 10_000),
+    ("2M x 1024 random walk", 2_000_000, 1024, "rw", 10_000),
+]
+
+
+def collection(kind: str, N: int, n: int, seed: int, device="cpu"):
+    """A collection of the served mix's kinds: 'rw' (z-normalised random
+    walks), 'gauss' (N(0,1) rows) or 'gauss_l2' (the same, L2-normalised)."""
+    if kind == "rw":
+        return random_walk(N, n, seed=seed, device=device)
+    return gaussian(N, n, seed=seed, device=device, l2=(kind == "gauss_l2"))
+
+
+def query_norm(kind: str):
+    """How queries of a collection kind are normalised (as its rows are)."""
+    return {"rw": "z", "gauss_l2": "l2", "gauss": None}[kind]
+
+
 def uniform_sigmas(nq: int, lo: float, hi: float, seed: int = 1):
     """nq noise levels drawn uniformly from [lo, hi]."""
     g = torch.Generator(device="cpu")
