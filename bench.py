@@ -49,13 +49,28 @@ WORKLOADS = {
                   desc="100K random walks x 256, leaf 1K, 10 queries (sigma 0.1), k=1"),
 }
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
-# capture committed under profiles/ (named beside each entry); a workload or
-# form without one reports traffic null.  Re-take them when the kernel changes.
-DRAM_TRAFFIC = {   # (workload, form, queries per step)
-    ("large", "fp16", 2000): dict(exact=62.74e9, approx=23.08e9,
-                                  source="profiles/k_tc_scan_dram_100M_x256_fp16.md"),
-}
+# DRAM traffic of the dominant kernel per launch, as a multiple of the
+# launch's algorithmic DRAM bytes (for k_tc_scan: the 16-bit rows and norms of
+# every leaf the step scans, each once), from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a small case of the same
+# shape; a full launch's traffic is that multiple of its own algorithmic bytes.
+# Each entry holds the SHA-256 prefix of the kernel source it was taken on;
+# once the source differs, traffic is reported as null until re-captured.
+TRAFFIC_RATIO = {}   # (kernel, form): dict(exact=r, approx=r, src=sha16, capture=description)
+KERNEL_SOURCE = {"k_tc_scan": "paper_2212_13297_gb300/csrc/hk_tc.cu",
+                 "k_scan": "paper_2212_13297_gb300/csrc/hk_query.cu"}
+
+
+def source_sha(kernel):
+    import hashlib
+    with open(os.path.join(ROOT, KERNEL_SOURCE[kernel]), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_ratio(kernel, form):
+    r = TRAFFIC_RATIO.get((kernel, form))
+    return r if r and r["src"] == source_sha(kernel) else None
+
 
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
@@ -224,16 +239,17 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def serve(binding, idx, Q_all, k, max_batch, qflags, args):
-    """Open-loop serving: requests arrive one query at a time (Poisson, rate
-    args.serve) and are answered by the continuous-batching server; reports
-    arrival-to-answer latency and the rate at which answers came back."""
+def serve(binding, idx, Q_all, k, max_batch, qflags, rate, seconds, form):
+    """Open-loop serving: requests arrive one query at a time (Poisson at
+    `rate` requests/s for `seconds`) and are answered by the
+    continuous-batching server; reports arrival-to-answer latency and the
+    rate at which answers came back."""
     import threading
     import numpy as np
     Qh = Q_all.cpu().numpy()
     rng = np.random.default_rng(11)
-    n_req = max(1, int(args.serve * args.serve_seconds))
-    gaps = rng.exponential(1.0 / args.serve, n_req)
+    n_req = max(1, int(rate * seconds))
+    gaps = rng.exponential(1.0 / rate, n_req)
     sv = binding.Server(max_batch=max_batch, max_wait_us=0, query_flags=qflags, workers=2)
     coll = sv.add(idx)
     # warm the workers' buffers
@@ -274,21 +290,13 @@ def serve(binding, idx, Q_all, k, max_batch, qflags, args):
     st = sv.stats()
     sv.close()
     ls = np.sort(lat)
-    return dict(kind="open loop, Poisson arrivals, one query per request, 2 workers",
-                offered_rate=args.serve, requests=n_req, answered_per_s=n_req / wall,
+    return dict(kind="open loop, Poisson arrivals, one query per request, 2 workers", form=form,
+                offered_rate=rate, requests=n_req, answered_per_s=n_req / wall,
                 latency_ms=dict(p50=float(ls[n_req // 2]) * 1e3,
                                 p99=float(ls[min(n_req - 1, int(0.99 * n_req))]) * 1e3,
                                 max=float(ls[-1]) * 1e3),
                 batches=st["batches"], mean_batch=st["served"] / max(1, st["batches"]),
                 max_batch=st["max_batch"], errors=st["errors"])
-
-
-MIX = [  # the served mix: name, N, n, kind, leaf capacity
-    ("20M x 96 Gaussian, L2-normalised", 20_000_000, 96, "gauss_l2", 10_000),
-    ("10M x 128 Gaussian", 10_000_000, 128, "gauss", 10_000),
-    ("10M x 256 random walk", 10_000_000, 256, "rw", 10_000),
-    ("2M x 1024 random walk", 2_000_000, 1024, "rw", 10_000),
-]
 
 
 def serve_mix(args):
@@ -306,16 +314,13 @@ def serve_mix(args):
     rng = np.random.default_rng(2)
     sv_flags = binding.HK_Q_BF16
     idxs, pools, builds = [], [], []
+    MIX = workload.SERVED_MIX
     for ci, (name, N, n, kind, tau) in enumerate(MIX):
         t0 = time.perf_counter()
-        if kind == "rw":
-            X = workload.random_walk(N, n, seed=10 + ci, device="cuda")
-        else:
-            X = workload.gaussian(N, n, seed=10 + ci, device="cuda", l2=(kind == "gauss_l2"))
+        X = workload.collection(kind, N, n, seed=10 + ci, device="cuda")
         nqp = 2048
         sig = workload.uniform_sigmas(nqp, 0.01, 1.0, seed=20 + ci)
-        norm = {"rw": "z", "gauss_l2": "l2", "gauss": None}[kind]
-        Q, _ = workload.queries(X, nqp, sig, seed=20 + ci, norm=norm)
+        Q, _ = workload.queries(X, nqp, sig, seed=20 + ci, norm=workload.query_norm(kind))
         flags = binding.HK_BUILD_FP16 if n <= 256 else 0
         idxs.append(binding.Index(X, tau, flags=flags))
         pools.append(Q.cpu().numpy())
@@ -504,10 +509,15 @@ def main():
                     help="query groups of the float32 measurements (0 = the library's choice)")
     ap.add_argument("--form", default="fp16", choices=["plain", "bf16", "fp16"],
                     help="plain float32 scan, or the tensor-core form on a bfloat16 / float16 copy")
-    ap.add_argument("--serve", type=float, default=0.0,
-                    help="also drive the continuous-batching server with Poisson arrivals at this "
-                         "rate (requests/s) and report arrival-to-answer latency")
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve", type=float, default=2000.0,
+                    help="also drive the continuous-batching server with the headline form at this "
+                         "Poisson arrival rate (requests/s) and report arrival-to-answer latency (0: off)")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-plain", type=float, default=500.0,
+                    help="the same for the float32 path, at a rate it sustains (0: off)")
+    ap.add_argument("--serve-plain-seconds", type=float, default=2.5)
+    ap.add_argument("--timing-steps", type=int, default=3,
+                    help="instrumented steps (kernel times by CUDA events) after the timed steps")
     ap.add_argument("--ablation", action="store_true",
                     help="instead of the step benchmark, the NoSAX / NoThresh ablation on the mid workload")
     ap.add_argument("--tune-graph", action="store_true",
@@ -562,7 +572,7 @@ def main():
         sample = X[:min(N, 4_000_000)].cpu().numpy()
     t0 = time.perf_counter()
     bflags = {"plain": 0, "bf16": binding.HK_BUILD_BF16, "fp16": binding.HK_BUILD_FP16}[args.form]
-    qflags = binding.HK_Q_TIMING | (binding.HK_Q_BF16 if args.form != "plain" else 0)
+    qflags = binding.HK_Q_BF16 if args.form != "plain" else 0
     idx = binding.Index(X, wl["tau"], flags=bflags)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
@@ -577,7 +587,9 @@ def main():
     qkw = dict(l_max=args.l_max, query_group=args.query_group, series_tile=args.series_tile)
 
     def timed(flags, steps, warmup, first, **over):
-        """Device time of `steps` batches (after `warmup`), summed stats, per-step latencies."""
+        """Device time of `steps` batches (after `warmup`), summed stats, and
+        each step's time between CUDA events recorded on the query stream
+        before and after its call (ms)."""
         kw = dict(qkw, **over)
         for i in range(warmup):
             idx.query(batches[rank_batch(first + i, rank, len(batches))], k, flags=flags,
@@ -586,30 +598,31 @@ def main():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         stream = torch.cuda.current_stream()
-        ev0.record(stream)
-        lat, agg = [], {}
+        evs[0].record(stream)
+        agg = {}
         for i in range(steps):
-            ts = time.perf_counter()
             _, _, st = idx.query(batches[rank_batch(first + warmup + i, rank, len(batches))], k,
                                  flags=flags, out=(ids, dist_out), **kw)
-            lat.append(time.perf_counter() - ts)
+            evs[i + 1].record(stream)
             for key, v in st.items():
                 agg[key] = agg.get(key, 0) + v
-        ev1.record(stream)
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-        t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws)
-        return t, agg, lat
+        t = max_over_ranks(evs[0].elapsed_time(evs[-1]) / 1e3, ws)
+        return t, agg, [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
 
     sampler = ClockSampler(dev_index)
     sampler.start()
-    t_dev, agg, step_lat = timed(qflags, args.steps, args.warmup, 0)
+    time.sleep(1.0)   # nvidia-smi starts up and takes its first samples before the timed region
+    t_dev, agg, step_ms = timed(qflags, args.steps, args.warmup, 0)
     clocks = sampler.stop()
     value = ws * B * args.steps / t_dev
+    # kernel times (CUDA events around the scan launches) from a separate,
+    # instrumented pass over the same batches, so the headline carries none
+    t_ins, agg_ins, _ = timed(qflags | binding.HK_Q_TIMING, args.timing_steps, 0, args.warmup)
 
     # end to end through the C ABI with host buffers (pinned queries in,
     # host results out; the copies are inside each call)
@@ -624,7 +637,7 @@ def main():
             torch.distributed.barrier()
         te = time.perf_counter()
         for i in range(args.steps):
-            idx.query(hq[i], k, flags=qflags & ~binding.HK_Q_TIMING, out=(hid, hdi), **qkw)
+            idx.query(hq[i], k, flags=qflags, out=(hid, hdi), **qkw)
         t_e2e = max_over_ranks(time.perf_counter() - te, ws)
         e2e = dict(value=ws * B * args.steps / t_e2e, unit="queries/s",
                    h2d_bytes_per_step=B * n * 4, d2h_bytes_per_step=B * k * 12)
@@ -644,8 +657,17 @@ def main():
                                query_group=gsz or "auto (8)")
             plain_runs.append((name, aggp))
 
-    serving = serve(binding, idx, Q_all, k, B, qflags & ~binding.HK_Q_TIMING, args) \
-        if args.serve > 0 else None
+    # served: Poisson arrivals through the continuous-batching server, the
+    # headline form and the float32 path at a rate it sustains
+    serving = None
+    if args.serve > 0 or args.serve_plain > 0:
+        serving = {}
+        if args.serve > 0:
+            serving[args.form] = serve(binding, idx, Q_all, k, B, qflags, args.serve, args.serve_seconds,
+                                       args.form)
+        if args.serve_plain > 0 and args.form != "plain":
+            serving["plain"] = serve(binding, idx, Q_all, k, B, 0, args.serve_plain,
+                                     args.serve_plain_seconds, "plain")
 
     if rank != 0:
         return
@@ -663,7 +685,7 @@ def main():
                     share_of_step=None)
 
     if args.form == "plain":
-        pr = plain_roof(agg)
+        pr = plain_roof(agg_ins)
         if pr["alu"]["frac"] >= pr["hbm"]["frac"]:
             roof = dict(bound="alu", achieved=pr["alu"]["achieved"], peak=alu_peak, unit="TFLOP/s",
                         frac=pr["alu"]["frac"], traffic=None, kernel="k_scan",
@@ -673,32 +695,36 @@ def main():
             roof = dict(bound="hbm", achieved=pr["hbm"]["achieved"], peak=pk["hbm_gbs"], unit="GB/s",
                         frac=pr["hbm"]["frac"], traffic=None, kernel="k_scan",
                         peak_note="of measured (%s)" % pk["source"])
-        roof["kernel_share_of_step"] = agg["scan_ns"] / 1e9 / t_dev
+        roof["kernel_share_of_step"] = agg_ins["scan_ns"] / 1e9 / t_ins
         for name, a in plain_runs:
             roof[name + "_k_scan"] = plain_roof(a)
     else:
-        tc_s = agg["tc_ns"] / 1e9
-        flops = 2.0 * n * agg["tc_pairs"]
+        a = agg_ins
+        tc_s = a["tc_ns"] / 1e9
+        flops = 2.0 * n * a["tc_pairs"]
         ach = flops / tc_s / 1e12 if tc_s else None
         peak_t = pk.get("bf16_tflops_sustained") or 1713.1
-        dram = DRAM_TRAFFIC.get((args.workload, args.form, B))
+        tr = traffic_ratio("k_tc_scan", args.form)
+        alg = a.get("tc_leaf_bytes", 0) / args.timing_steps
         roof = dict(bound="tensor", achieved=ach, peak=peak_t, unit="TFLOP/s", frac=(ach or 0) / peak_t,
-                    traffic=dram["exact"] if dram else None, kernel="k_tc_scan",
-                    traffic_note=("DRAM bytes per exact-step launch (%s)" % dram["source"]) if dram else None,
-                    algorithmic_dram_bytes_per_launch=agg.get("tc_leaf_bytes", 0) / args.steps,
+                    traffic=tr["exact"] * alg if tr else None, kernel="k_tc_scan",
+                    traffic_note=("DRAM bytes per exact-step launch: %.3f x its algorithmic bytes, the ratio "
+                                  "of an ncu capture of %s" % (tr["exact"], tr["capture"])) if tr else
+                                 "no DRAM capture of this kernel source",
+                    algorithmic_dram_bytes_per_launch=alg,
                     peak_note="of measured sustained bf16 (%s); %s dense rate equals bf16's nominally; "
                               "2n flops per (query, series) pair" % (pk["source"], args.form),
                     frac_of_burst=(ach or 0) / (pk.get("bf16_tflops") or 1920.7),
-                    hbm_side=dict(achieved=agg["tc_bytes"] / tc_s / 1e9 if tc_s else None,
-                                  peak=pk["hbm_gbs"], unit="GB/s",
-                                  note="16-bit rows + norms copied per query block (L2 serves repeats)"),
-                    kernel_share_of_step=tc_s / t_dev)
-        tca_s = agg.get("tc_approx_ns", 0) / 1e9
+                    bulk_copy_rate=dict(achieved=a["tc_bytes"] / tc_s / 1e9 if tc_s else None, unit="GB/s",
+                                        note="16-bit rows + norms the bulk copies move per query block, "
+                                             "served by L2 and DRAM together (not an HBM figure)"),
+                    kernel_share_of_step=tc_s / t_ins, timing_steps=args.timing_steps)
+        tca_s = a.get("tc_approx_ns", 0) / 1e9
         if tca_s:
             roof["approx_step_launches"] = dict(
-                kernel="k_tc_scan", share_of_step=tca_s / t_dev,
-                hbm_side=dict(achieved=agg["tc_approx_bytes"] / tca_s / 1e9, peak=pk["hbm_gbs"], unit="GB/s"),
-                traffic=dram["approx"] if dram else None,
+                kernel="k_tc_scan", share_of_step=tca_s / t_ins,
+                bulk_copy_rate=dict(achieved=a["tc_approx_bytes"] / tca_s / 1e9, unit="GB/s"),
+                traffic=tr["approx"] * a.get("tc_approx_bytes", 0) / args.timing_steps if tr else None,
                 note="the same kernel on each query's approximate-search leaves (few queries per "
                      "leaf: bound by the 16-bit rows it streams, not by the MMA)")
         for name, a in plain_runs:
@@ -713,7 +739,7 @@ def main():
                    sample="%d queries (blocks of %d) x first %d series (%.1f s of CPU), time scaled to "
                           "%d series" % (nqs, nqb, rows, dt, N))
 
-    lat = sorted(step_lat)
+    lat = sorted(step_ms)
     dtype = {"plain": "f32", "bf16": "bf16", "fp16": "fp16"}[args.form]
     line = dict(
         metric=metric_name(wl),
@@ -727,8 +753,10 @@ def main():
                          + " + exact float32/binary64 rescore",
                     parallelism="replicas" if ws > 1 else "1 GPU",
                     l2="inputs larger than L2 (%.0f GB collection)" % (N * n * 4 / 1e9)),
-        latency_ms=dict(kind="batch completion (closed loop, %d queries per batch)" % B,
-                        p50=lat[len(lat) // 2] * 1e3, p99=lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3),
+        latency_ms=dict(kind="batch completion (closed loop, %d queries per batch; CUDA events between "
+                             "consecutive calls on the query stream)" % B,
+                        p50=lat[len(lat) // 2], p99=lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                        per_step=[round(x, 3) for x in step_ms]),
         clocks=clocks, e2e=e2e, gpu_launches=agg["kernel_launches"], roofline=roof,
         cpu_baseline=cpu, forms=forms, serving=serving,
         pruning=dict(leaves_candidate_frac=agg["leaves_candidate"] / max(1, agg["leaves_total"]),

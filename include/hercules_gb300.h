@@ -178,6 +178,16 @@ typedef struct {
 } hk_query_stats;
 
 /*
+ * hk_query_opts_default -- write the options that opts = NULL stands for,
+ * with every "0 / < 0 = default" field resolved: l_max = 1 (Sec. 3.4,
+ * Approx-kNN step 1: one leaf by default), eapca_th = 0.25 and sax_th = 0.50
+ * (the thresholds of Sec. 4.2, Parameterization), flags 0, query_group and
+ * series_tile 0 (chosen per call).  Host-only; needs no GPU.  HK_EINVAL if
+ * out is NULL.
+ */
+int hk_query_opts_default(hk_query_opts *out);
+
+/*
  * hk_query -- exact k-NN (Sec. 3.4, Algorithm Exact-kNN and its steps
  * Approx-kNN, FindCandidateLeaves, CSWorker, CRWorker), for nq queries
  * answered together.
@@ -220,8 +230,15 @@ int hk_scan_knn(const float *X, int64_t N, int32_t n, const float *Q,
  * library, held on every GPU that loads it until the process exits.
  * Limits: 1 <= nq <= 64, 1 <= k <= min(N, 64), and at most 65,536
  * near-tied candidates per query; larger sizes return HK_EINVAL (HK_ENOMEM
- * for the tie limit) with a message.  The first call on a device looks up
- * the array's device address and should come before any stream capture.
+ * for the tie limit) with a message.  Each query pools at most 4,096
+ * candidates (hk_scan_knn pools max(4,096, 64 * (k + 32 rounded up to 32)),
+ * more once k > 32): a query with more near-ties than its pool holds is
+ * finished by an exhaustive collect, so for k > 32 near-tied queries take
+ * that slower path more often here than in hk_scan_knn (same answers).
+ * The first call on a device looks up the array's device address and
+ * should come before any stream capture; the address is kept for the life
+ * of the process, so resetting a device (cudaDeviceReset) after that first
+ * call is not supported.
  * All calls share the array and it keeps the last call's contents (each
  * call clears what must start at zero): calls whose GPU work overlaps, on
  * different streams or host threads, race on it.
@@ -353,6 +370,36 @@ int hk_debug_lb_sax(hk_index *idx, const float *Q, int32_t nq, float *out);
  * minus / plus its error bound.  Host outputs.
  */
 int hk_debug_tc_dist(hk_index *idx, const float *Q, int32_t nq, float *lo, float *up);
+
+/* ---- test hooks: no counterpart in the paper; they exist so the tests can
+ *      check the library's resource and failure behaviour ---------------- */
+
+/*
+ * hk_debug_device_allocs -- *count = device allocations (cudaMalloc calls)
+ * the library has made in this process so far, over all indexes, work
+ * spaces and calls.  Host-only; HK_EINVAL if count is NULL.
+ */
+int hk_debug_device_allocs(int64_t *count);
+
+/*
+ * hk_debug_fail_device_alloc -- arm a one-shot failure: the library's
+ * (after+1)-th device allocation from now fails as a failed cudaMalloc
+ * would (the call returns HK_ENOMEM and releases what it allocated);
+ * after < 0 disarms.  Process-wide; for tests of HK_ENOMEM handling.
+ */
+int hk_debug_fail_device_alloc(int64_t after);
+
+/*
+ * hk_debug_tc_wait -- the tensor-core scan's bounded waits (each mbarrier
+ * wait of its producer, MMA and epilogue roles gives up after a limit and
+ * the call returns HK_ETIMEOUT): limit_ns sets that limit for later calls
+ * (0 = the default, 2 s); stall != 0 makes one epilogue warp of each CTA
+ * wait, at its first work item, for a barrier nothing arrives at, so that
+ * its wait runs out.  An aborting CTA waits (up to 200 ms) for its copies
+ * and tensor-core operations in flight and frees its tensor memory before
+ * it exits.  Process-wide; for tests.
+ */
+int hk_debug_tc_wait(uint64_t limit_ns, int32_t stall);
 
 const char *hk_last_error(void);
 const char *hk_version(void);

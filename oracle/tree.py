@@ -235,3 +235,99 @@ def leaf_synopsis(X, leaf):
         env[j] = (mu.min(), mu.max(), sd.min(), sd.max())
         a = b
     return env
+
+
+def nodes_preorder(root):
+    """Every node, parents before children, left subtree before right."""
+    out = []
+    stack = [root]
+    while stack:
+        node = stack.pop()
+        out.append(node)
+        if not node.is_leaf:
+            stack.append(node.right)
+            stack.append(node.left)
+    return out
+
+
+def subtree_members(node):
+    """Ids of every series in the node's subtree (the series that traversed
+    it), in inorder leaf order."""
+    return [i for leaf in leaves_inorder(node) for i in leaf.members]
+
+
+def node_synopsis(X, node):
+    """Synopsis of any node by its definition (Sec. 3.3): for every segment of
+    the node's own segmentation, the min / max of the mean and of the std over
+    all series that traversed the node, as an [m, 4] binary64 array."""
+    rows = np.asarray(subtree_members(node), dtype=np.int64)
+    env = np.empty((len(node.seg_end), 4), dtype=np.float64)
+    a = 0
+    for j, b in enumerate(node.seg_end):
+        mu, sd = seg_stats_rows(X, rows, a, b)
+        env[j] = (mu.min(), mu.max(), sd.min(), sd.max())
+        a = b
+    return env
+
+
+def fold_synopses(X, root):
+    """Synopses of every node as the paper's post-processing of each leaf
+    computes them (Sec. 3.3, Algorithms ProcessLeaf, VSplitSynopsis and
+    HSplitSynopsis), leaf by leaf in inorder:
+      * each leaf's own synopsis comes from its series (insertion keeps it);
+      * VSplitSynopsis, per series of the leaf: every ancestor whose split
+        was vertical updates the segment it split (its own segmentation's
+        segment) with the series' mean and std over that segment;
+      * HSplitSynopsis, once per leaf: walking up from the leaf, each parent
+        updates every segment it did not split vertically with the min / max
+        of the corresponding segment (same end points) of the child on the
+        path.
+    Returns {id(node): [m, 4] array}."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    parent = {}
+    for node in nodes_preorder(root):
+        if not node.is_leaf:
+            parent[id(node.left)] = node
+            parent[id(node.right)] = node
+    syn = {}
+    for node in nodes_preorder(root):
+        m = len(node.seg_end)
+        syn[id(node)] = np.tile(np.array([np.inf, -np.inf, np.inf, -np.inf]), (m, 1))
+
+    def upd(z, mu, sd):
+        z[0] = min(z[0], mu)
+        z[1] = max(z[1], mu)
+        z[2] = min(z[2], sd)
+        z[3] = max(z[3], sd)
+
+    for leaf in leaves_inorder(root):
+        syn[id(leaf)] = leaf_synopsis(X, leaf)
+        for i in leaf.members:                           # VSplitSynopsis
+            node = parent.get(id(leaf))
+            while node is not None:
+                if node.policy.kind == "V":
+                    j = node.policy.seg
+                    a = 0 if j == 0 else node.seg_end[j - 1]
+                    mu, sd = seg_stats(X[i], a, node.seg_end[j])
+                    upd(syn[id(node)][j], mu, sd)
+                node = parent.get(id(node))
+        child = leaf                                     # HSplitSynopsis
+        node = parent.get(id(leaf))
+        while node is not None:
+            vseg = node.policy.seg if node.policy.kind == "V" else -1
+            cz = syn[id(child)]
+            a = 0
+            for j, b in enumerate(node.seg_end):
+                if j != vseg:
+                    jc = child.seg_end.index(b)          # the child's segment ending at b
+                    ac = 0 if jc == 0 else child.seg_end[jc - 1]
+                    assert ac == a, "child segment does not match the parent's"
+                    z = syn[id(node)][j]
+                    z[0] = min(z[0], cz[jc][0])
+                    z[1] = max(z[1], cz[jc][1])
+                    z[2] = min(z[2], cz[jc][2])
+                    z[3] = max(z[3], cz[jc][3])
+                a = b
+            child = node
+            node = parent.get(id(node))
+    return syn

@@ -96,7 +96,8 @@ EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_scan_knn"
            "hk_isax_breakpoints", "hk_index_export", "hk_debug_lb_eapca", "hk_debug_lb_sax",
            "hk_debug_tc_dist", "hk_server_create", "hk_server_add", "hk_submit", "hk_poll",
            "hk_server_stats_get", "hk_server_destroy", "hk_tune", "hk_save", "hk_load",
-           "hk_last_error", "hk_version"]
+           "hk_query_opts_default", "hk_debug_device_allocs", "hk_debug_fail_device_alloc",
+           "hk_debug_tc_wait", "hk_last_error", "hk_version"]
 
 
 def lib():
@@ -137,6 +138,10 @@ def lib():
                               ctypes.POINTER(hk_tune_result)]
         L.hk_save.argtypes = [vp, ctypes.c_char_p]
         L.hk_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
+        L.hk_query_opts_default.argtypes = [ctypes.POINTER(hk_query_opts)]
+        L.hk_debug_device_allocs.argtypes = [i64p]
+        L.hk_debug_fail_device_alloc.argtypes = [ctypes.c_int64]
+        L.hk_debug_tc_wait.argtypes = [ctypes.c_uint64, ctypes.c_int32]
         L.hk_last_error.restype = ctypes.c_char_p
         L.hk_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -170,6 +175,20 @@ def _stream(stream):
     except Exception:
         pass
     return ctypes.c_void_p(0)
+
+
+def query_opts_default():
+    """The options a NULL hk_query_opts stands for, as a dict."""
+    o = hk_query_opts()
+    _check(lib().hk_query_opts_default(ctypes.byref(o)))
+    return {f[0]: getattr(o, f[0]) for f in o._fields_}
+
+
+def device_allocs():
+    """Device allocations the library has made in this process so far."""
+    c = ctypes.c_int64()
+    _check(lib().hk_debug_device_allocs(ctypes.byref(c)))
+    return c.value
 
 
 def isax_breakpoints():

@@ -4,9 +4,36 @@
 
 #include "hk_internal.cuh"
 
+#include <atomic>
+
 namespace hk {
 const char *last_error_cstr();
+
+namespace {
+std::atomic<long long> g_device_allocs{0};   // DevBuf allocations in this process
+std::atomic<long long> g_fail_after{-1};     // armed: allocations left before one fails
+std::atomic<unsigned long long> g_tc_wait_ns{0};
+std::atomic<int> g_tc_stall{0};
+}  // namespace
+
+void note_device_alloc(size_t bytes) {
+    g_device_allocs.fetch_add(1);
+    long long f = g_fail_after.load();
+    while (f >= 0) {
+        if (g_fail_after.compare_exchange_weak(f, f - 1)) {
+            if (f == 0)
+                fail(HK_ENOMEM, "device allocation of %zu bytes failed (injected by "
+                                "hk_debug_fail_device_alloc)", bytes);
+            break;
+        }
+    }
 }
+
+void tc_wait_hooks(uint64_t &wait_ns, int &stall) {
+    wait_ns = g_tc_wait_ns.load();
+    stall = g_tc_stall.load();
+}
+}  // namespace hk
 
 namespace {
 
@@ -49,6 +76,34 @@ extern "C" {
 const char *hk_version(void) { return "hercules-gb300 0.1 (sm_103a)"; }
 
 const char *hk_last_error(void) { return hk::last_error_cstr(); }
+
+int hk_query_opts_default(hk_query_opts *out) {
+    return guard([&] {
+        if (!out) hk::fail(HK_EINVAL, "out is NULL");
+        std::memset(out, 0, sizeof(*out));
+        out->l_max = hk::kDefaultLMax;
+        out->eapca_th = hk::kDefaultEapcaTh;
+        out->sax_th = hk::kDefaultSaxTh;
+    });
+}
+
+int hk_debug_device_allocs(int64_t *count) {
+    return guard([&] {
+        if (!count) hk::fail(HK_EINVAL, "count is NULL");
+        *count = hk::g_device_allocs.load();
+    });
+}
+
+int hk_debug_fail_device_alloc(int64_t after) {
+    return guard([&] { hk::g_fail_after.store(after < 0 ? -1 : after); });
+}
+
+int hk_debug_tc_wait(uint64_t limit_ns, int32_t stall) {
+    return guard([&] {
+        hk::g_tc_wait_ns.store(limit_ns);
+        hk::g_tc_stall.store(stall ? 1 : 0);
+    });
+}
 
 int hk_isax_breakpoints(float out[255]) {
     return guard([&] {

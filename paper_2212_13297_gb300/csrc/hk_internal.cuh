@@ -16,6 +16,12 @@ constexpr int kRootSegments = 4;     // root segmentation: 4 equal segments
 constexpr int kWord = HK_ISAX_SEGMENTS;
 constexpr int kAlpha = HK_ISAX_ALPHABET;
 constexpr int kDefaultEvalCap = 4096;
+// Query parameters a zero / negative option stands for: L_max is 1 by
+// default (Sec. 3.4, Approx-kNN step 1); EAPCA_TH 0.25 and SAX_TH 0.50 are
+// the values of the paper's experiments (Sec. 4.2, Parameterization).
+constexpr int kDefaultLMax = 1;
+constexpr float kDefaultEapcaTh = 0.25f;
+constexpr float kDefaultSaxTh = 0.50f;
 
 // ---------------------------------------------------------------- errors
 struct Error {
@@ -43,6 +49,11 @@ extern thread_local long long g_launches;   // kernels launched by this thread
     } while (0)
 
 // ---------------------------------------------------------------- device memory
+// Every device allocation of the library goes through DevBuf::alloc, which
+// counts it (hk_debug_device_allocs) and fails it with HK_ENOMEM when a test
+// armed a failure (hk_debug_fail_device_alloc).
+void note_device_alloc(size_t bytes);
+
 // Owning device buffer.  cudaMalloc/cudaFree: cudaFree waits for the device,
 // so a buffer can be released whichever stream last used it.
 template <class T>
@@ -65,6 +76,7 @@ struct DevBuf {
     void alloc(size_t count, cudaStream_t = nullptr) {
         release();
         if (count == 0) return;
+        note_device_alloc(count * sizeof(T));
         HK_CHECK_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
         n = count;
     }
@@ -196,6 +208,24 @@ struct hk_index {
     std::vector<int32_t> h_leaf_nseg;
     std::vector<int32_t> h_seg_end;   // L*kMaxSeg
 
+    // The whole tree (HTree, Sec. 3.3).  Node ids: leaves 0..L-1 in leaf
+    // (inorder) order, internal nodes L..T-1, parents before children; every
+    // split makes two children, so T = 2L - 1.  A node's series occupy the
+    // leaf-order positions [tree_beg, tree_end).
+    int64_t T = 0;
+    std::vector<int32_t> h_tree_parent, h_tree_left, h_tree_right, h_tree_level;   // T
+    std::vector<int64_t> h_tree_beg, h_tree_end;                                   // T
+    std::vector<int32_t> h_inode_nseg;       // T - L
+    std::vector<int32_t> h_inode_seg_end;    // (T - L) * kMaxSeg
+    std::vector<int32_t> h_inode_seg;        // (T - L) * kMaxSeg distinct-segment ids
+    hk::DevBuf<int32_t> tree_parent, tree_left, tree_right;   // T
+    hk::DevBuf<int64_t> tree_beg, tree_end;                   // T
+    hk::DevBuf<int32_t> inode_nseg;          // T - L
+    hk::DevBuf<int32_t> inode_seg;           // (T - L) * kMaxSeg distinct-segment ids
+    hk::DevBuf<double> ienv;                 // (T - L) * kMaxSeg * 4 internal synopses
+    std::vector<int32_t> h_level_off;        // depth + 2: nodes of level d are
+    hk::DevBuf<int32_t> level_nodes;         //   level_nodes[h_level_off[d] .. h_level_off[d+1])
+
     hk::Workspace ws;
     hk::Workspace ws_retry;
     hk::Workspace ws_graph;    // HK_Q_GRAPH calls only: its buffers stay where the graph points
@@ -205,6 +235,9 @@ namespace hk {
 // Build (hk_build.cu)
 void build_index(hk_index *idx, const float *X, int64_t N, int n, const hk_build_opts &o,
                  cudaStream_t s);
+// Device copies of the tree arrays (from the h_tree_* / h_inode_* vectors);
+// sizes ienv (filled by the caller).  Also forms the level lists.
+void upload_tree(hk_index *idx, cudaStream_t s);
 // Query (hk_query.cu)
 void run_query(hk_index *idx, const float *Qdev, int nq, int k, const hk_query_opts &o,
                cudaStream_t s, int64_t *out_ids_host_or_dev, float *out_dist_host_or_dev,
@@ -273,7 +306,12 @@ struct TcArgs {
     uint32_t idesc;
     float *dbg_lo, *dbg_up;      // if set: certified interval of every pair, [q * N + pos]
     int64_t N;
+    uint64_t wait_ns;            // limit of each bounded wait (0: the default, 2 s)
+    int dbg_stall;               // test hook: one epilogue warp per CTA waits for a barrier
+                                 // nothing arrives at, so its wait runs out (HK_ETIMEOUT)
 };
+// Test hooks of the tensor-core scan's bounded waits (hk_debug_tc_wait).
+void tc_wait_hooks(uint64_t &wait_ns, int &stall);
 void launch_tc_scan(const TcArgs &a, cudaStream_t s);
 constexpr int kFmtF16 = 0;    // tcgen05 kind::f16 operand encodings
 constexpr int kFmtBF16 = 1;

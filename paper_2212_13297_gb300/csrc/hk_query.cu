@@ -94,9 +94,9 @@ __device__ __forceinline__ float upper_f(float d, float rho) { return __fmul_ru(
 
 // --------------------------------------------------------------------------
 // a1: query preparation.  Per query: mean and std of every distinct leaf
-// segment (binary64, the build's exact definition), PAA over 16 segments, and
-// the LB_SAX table T[i][s] = (n/16) dist(PAA_i, cell s)^2 rounded down to
-// float16 (8 KB per query, so a scan CTA holds the tables of its queries).
+// segment (binary64, the build's exact definition) and the PAA over 16
+// segments (binary64) bracketed by the float32 values just below and just
+// above it, from which the scan forms LB_SAX rounded down.
 __global__ void k_qprep(const float *__restrict__ Q, int n, const int32_t *__restrict__ seg_ab,
                         int64_t S, double *__restrict__ qseg, float *__restrict__ paa_out) {
     extern __shared__ float qs[];
@@ -1219,6 +1219,7 @@ void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, 
     t.dbg_lo = nullptr;
     t.dbg_up = nullptr;
     t.N = idx->N;
+    tc_wait_hooks(t.wait_ns, t.dbg_stall);
     if (tctimer) tctimer->mark(s);
     launch_tc_scan(t, s);
     if (tctimer) tctimer->mark(s);
@@ -1414,8 +1415,8 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     const bool noprune = (o.flags & HK_Q_NOPRUNE) != 0;
     const bool tc = (o.flags & HK_Q_BF16) != 0;
     const bool nosax = noprune || tc || (o.flags & HK_Q_NOSAX) != 0;
-    const int l_max = o.l_max > 0 ? o.l_max : 1;
-    const float eapca_th = o.eapca_th >= 0 ? o.eapca_th : 0.25f;
+    const int l_max = o.l_max > 0 ? o.l_max : kDefaultLMax;
+    const float eapca_th = o.eapca_th >= 0 ? o.eapca_th : kDefaultEapcaTh;
     ScanConfig cfg = choose_scan(n, k, !nosax, o.query_group);
     const int S_T = o.series_tile > 0 ? o.series_tile : 8192;
     // the precision form's bound admits a band of near candidates around the

@@ -9,10 +9,30 @@
 // certified error bound E(q,x) = A_q |x| + B (|q|^2 + |x|^2):
 //   |q^.x^ - q.x| <= (2u + u^2 + g(1+u)^2) |q||x| + (subnormal term),
 //   u = 2^-8 (bfloat16) or 2^-11 (float16),
-//   g = n w / (1 - n w), w = 2^-20 (a pessimistic per-addition error of the
-//   float32 accumulation, allowing truncating adders),
+//   g = n w / (1 - n w), w = 2^-20,
 // doubled for the -2 factor, plus a relative term covering the float32
-// rounding of the norms and of the epilogue arithmetic.  A series stays a
+// rounding of the norms and of the epilogue arithmetic.
+//
+// Where g comes from.  Fasi, Higham, Mikaitis and Pranesh ("Numerical
+// behavior of NVIDIA tensor cores", PeerJ Computer Science 7:e330, 2021)
+// measured that tensor cores of earlier generations (V100, T4, A100) form
+// d = c + sum_{i<m} a_i b_i for a block of m products as follows: products
+// exact; the m + 1 addends aligned to the largest, with the bits below that
+// addend's 24-bit significand truncated; the aligned addends summed exactly;
+// the sum normalised to float32 by truncation.  The block size m and the
+// number of bits kept varied by generation; no published study covers
+// tcgen05.  The bound assumes the same family for any m >= 1 and at least
+// 24 kept bits.  Then one block step errs by less than (m+1) 2^-23 M for the
+// alignment plus 2^-23 |d| for the normalisation, where M is the largest
+// addend; both are at most P = sum |a_i b_i| over the whole dot product
+// (the accumulator holds a partial sum, itself bounded by P up to these
+// errors).  Over n/m steps the error is below (n/m)(m+2) 2^-23 P <=
+// 3 n 2^-23 P (worst at m = 1), and P <= |q^||x^| <= (1+u)^2 |q||x| by
+// Cauchy-Schwarz.  g >= n 2^-20 covers 3 n 2^-23 with a factor 8/3; it
+// still covers the case of only 22 kept bits when m >= 2.  The per-pair
+// bound is checked against binary64 distances on benign and adversarial
+// inputs (cancellation, alternating signs, values near the format's largest,
+// wide exponent ranges, the float16 subnormal range, n = 16 ... 256).  A series stays a
 // candidate of a query while D~ - E <= U (U bounds the query's true k-th
 // distance); D~ + E of k series bounds it from above, so each query's row
 // keeps its k smallest D~ + E and tightens U with them.  Candidates are
@@ -77,6 +97,7 @@ constexpr int kTmemA = kAcc * kTcN; // first column of the query block (n/2 <= 1
 static_assert(kTmemA + 128 <= kTmemCols, "tensor memory overflow");
 static_assert(kNormSlots >= kTcStages + kAcc + 1, "norm slot reuse distance");
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far above any legitimate wait
+constexpr uint64_t kDrainNs = 200000000ull;   // 200 ms for copies / MMAs in flight to land
 constexpr int kLocalK = kTcLocalK;   // k-best upper bounds kept per epilogue thread
 constexpr double kTcEb = 0x1p-19;   // relative term for norm and epilogue rounding
 constexpr float kF16Max = 65504.0f;      // largest finite float16: the float16 copy's range
@@ -111,22 +132,32 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 // Bounded wait for the phase with the given parity to complete: gives up
-// after kWaitNs of wall time or when the CTA is aborting (then returns
+// after limit_ns of wall time or when the CTA is aborting (then returns
 // false; on its own timeout it sets the abort flag).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint64_t limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if ((it & 255) == 0 && global_ns() - t0 > kWaitNs) {
+        if ((it & 255) == 0 && global_ns() - t0 > limit_ns) {
             *abort_flag = 1;
             return false;
         }
     }
 }
+// Wait for a phase without regard to the abort flag, until a deadline of
+// %globaltimer (the drain of an aborting CTA); false if the deadline passed.
+__device__ __forceinline__ bool mbar_wait_until(uint64_t *bar, uint32_t parity, uint64_t deadline) {
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 255 && global_ns() > deadline) return false;
+    }
+}
 // The same, decided once for a whole warp (every lane polls, all agree).
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                               uint64_t limit_ns) {
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
         const bool ok = mbar_try(bar, parity);
@@ -134,7 +165,7 @@ __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, v
         const bool stop = *abort_flag != 0;
         if (__any_sync(0xffffffffu, stop)) return false;
         if ((it & 255) == 255) {
-            const bool late = global_ns() - t0 > kWaitNs;
+            const bool late = global_ns() - t0 > limit_ns;
             if (__any_sync(0xffffffffu, late)) {
                 *abort_flag = 1;
                 return false;
@@ -226,6 +257,7 @@ struct TcShared {
     uint64_t empty[kTcStages];
     uint64_t acc_full[kAcc];
     uint64_t acc_empty[kAcc];
+    uint64_t never;        // test hook (dbg_stall): a barrier nothing arrives at
     uint32_t tmem_base;
     int abort_flag;
     TcItem item;
@@ -303,6 +335,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
             mbar_init(&S.acc_full[b], 1);
             mbar_init(&S.acc_empty[b], 32 * kTcEpiWarps);
         }
+        mbar_init(&S.never, 1);
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -322,6 +355,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
 
     // running counts of barrier completions (phases), kept per role
     uint32_t g_tile = 0;   // tiles processed by this CTA so far (all roles agree)
+    uint32_t issued = 0;   // producer: tiles whose copies it issued; MMA warp: tiles it committed
+    const uint64_t wait_ns = A.wait_ns ? A.wait_ns : kWaitNs;
     long long my_cand = 0, my_pairs = 0, my_bytes = 0;
 
     // Items are claimed when a CTA is ready for one, so the query blocks of
@@ -370,12 +405,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                     const uint32_t gt = g_tile + t;
                     const int s = gt % nst;
                     const uint32_t use = gt / nst;
-                    if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1, &S.abort_flag)) break;
+                    if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1, &S.abort_flag, wait_ns)) break;
                     const int64_t row0 = base + (int64_t)t * kTcN;
                     const uint32_t norm_bytes = kTcN * (uint32_t)sizeof(float2);
                     mbar_arrive_expect_tx(&S.full[s], b_bytes + norm_bytes);
                     bulk_g2s(sB + s * kTcStageBytes, A.Xb + row0 * n, b_bytes, &S.full[s]);
                     bulk_g2s(sX + (gt % kNormSlots) * kTcN, A.xq + row0, norm_bytes, &S.full[s]);
+                    issued = gt + 1;
                 }
             }
         } else if (warp == 1) {
@@ -389,8 +425,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                     const uint32_t use = gt / nst;
                     const int b = gt % kAcc;
                     const uint32_t ause = gt / kAcc;
-                    if (ause > 0 && !mbar_wait(&S.acc_empty[b], (ause - 1) & 1, &S.abort_flag)) break;
-                    if (!mbar_wait(&S.full[s], use & 1, &S.abort_flag)) break;
+                    if (ause > 0 && !mbar_wait(&S.acc_empty[b], (ause - 1) & 1, &S.abort_flag, wait_ns)) break;
+                    if (!mbar_wait(&S.full[s], use & 1, &S.abort_flag, wait_ns)) break;
                     tc_fence_after();
                     const uint32_t b_base = smem_u32(sB + s * kTcStageBytes);
                     const uint32_t d = tmem + (uint32_t)(b * kTcN);
@@ -401,6 +437,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                     }
                     mma_commit(&S.empty[s]);
                     mma_commit(&S.acc_full[b]);
+                    issued = gt + 1;
                 }
             }
         } else {
@@ -423,11 +460,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
             for (int i = 0; i < kl; ++i) kb[i * kTcEpiThreads] = INFINITY;
             float kth = INFINITY;      // k-th smallest upper bound seen by this thread
             long long pairs = 0;
-            for (int t = 0; t < T; ++t) {
+            // test hook: one epilogue warp waits for a barrier nothing
+            // arrives at, so its bounded wait runs out and the CTA aborts
+            const bool stalled = A.dbg_stall && warp == 2 && g_tile == 0 &&
+                                 !mbar_wait_warp(&S.never, 0, &S.abort_flag, wait_ns);
+            for (int t = 0; t < T && !stalled; ++t) {
                 const uint32_t gt = g_tile + t;
                 const int b = gt % kAcc;
                 const uint32_t ause = gt / kAcc;
-                if (!mbar_wait_warp(&S.acc_full[b], ause & 1, &S.abort_flag)) break;
+                if (!mbar_wait_warp(&S.acc_full[b], ause & 1, &S.abort_flag, wait_ns)) break;
                 tc_fence_after();
                 if (q >= 0 && (t & 7) == 0) U = fminf(U, __uint_as_float(A.U[q]));
                 const int64_t row0 = base + (int64_t)t * kTcN;
@@ -534,16 +575,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
         g_tile += T;
         __syncthreads();
     }
-    // drain: a CTA that aborted may have copies or MMAs in flight; wait for
-    // the last tile's barriers (bounded), then free the tensor memory.
+    // drain: a CTA that aborted may have copies or MMAs in flight.  The
+    // producer waits for the copies of the last kTcStages tiles it issued
+    // (earlier ones were consumed by the MMA warp, so they landed); the MMA
+    // warp waits for the commits of the last tile it issued (a commit
+    // arrives once every earlier MMA of the thread completed).  Each wait
+    // ends by a deadline; then the tensor memory is freed.
     if (S.abort_flag) {
         if (tid == 0) atomicOr(A.err, 2);
-        if (tid == 0 && g_tile > 0) {
-            // let in-flight bulk copies land before the CTA's memory goes away
-            const uint64_t t0 = global_ns();
-            while (global_ns() - t0 < 100000000ull) {
-            }
+        const uint64_t deadline = global_ns() + kDrainNs;
+        bool landed = true;
+        if (warp == 0 && lane == 0) {
+            for (uint32_t gt = issued > (uint32_t)nst ? issued - nst : 0; gt < issued; ++gt)
+                landed &= mbar_wait_until(&S.full[gt % nst], (gt / nst) & 1, deadline);
+        } else if (warp == 1 && lane == 0 && issued > 0) {
+            const uint32_t last = issued - 1;
+            landed &= mbar_wait_until(&S.empty[last % nst], (last / nst) & 1, deadline);
+            landed &= mbar_wait_until(&S.acc_full[last % kAcc], (last / kAcc) & 1, deadline);
         }
+        if (!landed) atomicOr(A.err, 4);
     }
     tc_fence_before();
     __syncthreads();

@@ -6,6 +6,8 @@ squared distance (binary64 from numpy, a separate implementation), so the
 candidate filter never drops a true neighbour.  Answers through the
 precision form must equal the brute-force oracle's.
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -151,3 +153,50 @@ def test_tc_edge_cases(hb, oracle_lib, fmt):
         oids, od2 = oracle.knn(X.cpu().numpy(), Q.cpu().numpy(), 7)
         np.testing.assert_array_equal(ids.cpu().numpy(), oids)
         np.testing.assert_allclose(dist.cpu().numpy(), np.sqrt(od2).astype(np.float32), rtol=1e-5)
+
+
+def _adversarial(kind, N, n, fmt, rng):
+    """Rows and queries that stress the float32 accumulation and the 16-bit
+    rounding: every pair's interval must still hold the exact distance."""
+    big = 2.0e4 if fmt == "fp16" else 1.0e15     # float16 holds up to 65504
+    if kind == "cancel":          # q ~ x with large norms: D << |q||x|
+        X = rng.standard_normal((N, n)) * big / 4
+        src = rng.integers(0, N, 24)
+        Q = X[src] * (1 + 1e-3 * rng.standard_normal((24, n)))
+    elif kind == "alternating":   # products alternate in sign along the sum
+        mag = np.abs(rng.standard_normal((N, n))) * big / 8
+        X = mag * np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+        Q = np.abs(rng.standard_normal((24, n))) * big / 8
+        Q[12:] *= np.where(np.arange(n) % 2 == 0, -1.0, 1.0)
+    elif kind == "near_max":      # magnitudes close to the format's largest
+        # bfloat16: large, yet squared distances stay inside float32's range
+        top = 65504.0 if fmt == "fp16" else 1.0e17
+        X = rng.choice([-1.0, 1.0], (N, n)) * rng.uniform(0.9, 1.0, (N, n)) * top
+        Q = rng.choice([-1.0, 1.0], (24, n)) * rng.uniform(0.9, 1.0, (24, n)) * top
+    elif kind == "wide_range":    # signs and binary exponents spread over 2^-12 .. 2^12
+        X = rng.choice([-1.0, 1.0], (N, n)) * np.exp2(rng.integers(-12, 13, (N, n)))
+        Q = rng.choice([-1.0, 1.0], (24, n)) * np.exp2(rng.integers(-12, 13, (24, n)))
+    elif kind == "tiny":          # float16 subnormal range and below
+        X = rng.standard_normal((N, n)) * 1e-6
+        Q = rng.standard_normal((24, n)) * 1e-6
+    else:
+        raise ValueError(kind)
+    return X.astype(np.float32), Q.astype(np.float32)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+@pytest.mark.parametrize("kind", ["cancel", "alternating", "near_max", "wide_range", "tiny"])
+@pytest.mark.parametrize("n", [16, 64, 256])
+def test_tc_bound_adversarial(hb, kind, n, fmt):
+    rng = np.random.default_rng(zlib.crc32(("%s/%d/%s" % (kind, n, fmt)).encode()))
+    X, Q = _adversarial(kind, 700, n, fmt, rng)
+    Xd = torch.from_numpy(X).cuda()
+    idx = hb.Index(Xd, 64, flags=hb.HK_BUILD_BF16 if fmt == "bf16" else hb.HK_BUILD_FP16)
+    ex = idx.export()
+    lo, up = idx.debug_tc_dist(torch.from_numpy(Q).cuda())
+    Xl = X.astype(np.float64)[ex["perm"]]
+    exact = ((Q.astype(np.float64)[:, None, :] - Xl[None, :, :]) ** 2).sum(-1)
+    assert not np.isnan(lo).any() and not np.isnan(up).any(), "some pairs were not computed"
+    lo64, up64 = lo.astype(np.float64), up.astype(np.float64)
+    assert (lo64 <= exact).all(), (kind, float((lo64 - exact).max()))
+    assert (up64 >= exact).all(), (kind, float((exact - up64).max()))

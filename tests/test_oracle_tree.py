@@ -170,3 +170,61 @@ def test_eval_cap_uses_first_members(oracle_lib):
     assert root.policy.seg == 1 and root.policy.threshold == 0.5
     root_full = otree.build_tree(X, 3, eval_cap=4096)
     assert root_full.policy.seg == 1      # at overflow only 4 series exist
+
+
+# ---- internal-node synopses (Sec. 3.3: ProcessLeaf, VSplitSynopsis, HSplitSynopsis)
+
+@pytest.mark.parametrize("N,n,tau,seed", [(600, 64, 20, 0), (400, 32, 8, 1), (300, 16, 5, 2)])
+def test_folded_synopses_equal_their_definition(oracle_lib, N, n, tau, seed):
+    from oracle import tree
+    rng = np.random.default_rng(seed)
+    X = np.cumsum(rng.standard_normal((N, n)), axis=1)
+    X = ((X - X.mean(1, keepdims=True)) / X.std(1, keepdims=True)).astype(np.float32)
+    root = tree.build_tree(X, tau)
+    syn = tree.fold_synopses(X, root)
+    nodes = tree.nodes_preorder(root)
+    assert sum(1 for nd in nodes if not nd.is_leaf) >= 5
+    for nd in nodes:
+        np.testing.assert_array_equal(syn[id(nd)], tree.node_synopsis(X, nd))
+
+
+def test_vsplit_fold_worked_example(oracle_lib):
+    """A parent that split its first segment [0, 4) vertically, with one
+    series in each child.  Over [0, 4) both series have mean 1 and std 1,
+    while over the halves each has std 0 and means 0 / 2: the parent's
+    synopsis of [0, 4) must come from the raw points (VSplitSynopsis), not
+    from the children's halves, whose union (means [0, 2], stds [0, 0])
+    would not even enclose the series."""
+    from oracle import tree
+    X = np.zeros((2, 16), np.float32)
+    X[0, :4] = [0, 0, 2, 2]
+    X[1, :4] = [2, 2, 0, 0]
+    child_seg = [2, 4, 8, 12, 16]
+    root = tree.Node([4, 8, 12, 16])
+    root.policy = tree.Policy("V", 0, 0, 0, 0, 2, 1.0)
+    root.left = tree.Node(list(child_seg), members=[0])
+    root.right = tree.Node(list(child_seg), members=[1])
+    expect = np.array([[1, 1, 1, 1], [0, 0, 0, 0], [0, 0, 0, 0], [0, 0, 0, 0]], np.float64)
+    syn = tree.fold_synopses(X, root)
+    np.testing.assert_array_equal(syn[id(root)], expect)
+    np.testing.assert_array_equal(tree.node_synopsis(X, root), expect)
+    np.testing.assert_array_equal(syn[id(root.left)][:2], [[0, 0, 0, 0], [2, 2, 0, 0]])
+
+
+def test_node_lb_bounds_every_member(oracle_lib):
+    """LB_EAPCA of a query to any node's synopsis is at most the distance to
+    each series of the node's subtree: pruning a whole subtree on its root's
+    bound is exact (Sec. 3.4)."""
+    import oracle
+    from oracle import tree
+    rng = np.random.default_rng(5)
+    X = np.cumsum(rng.standard_normal((300, 32)), axis=1)
+    X = ((X - X.mean(1, keepdims=True)) / X.std(1, keepdims=True)).astype(np.float32)
+    Q = X[rng.integers(0, 300, 6)] + rng.standard_normal((6, 32)).astype(np.float32)
+    root = tree.build_tree(X, 10)
+    for nd in tree.nodes_preorder(root):
+        env = tree.node_synopsis(X, nd)
+        for q in Q:
+            lb = oracle.lb_eapca(q, nd.seg_end, env)
+            for i in tree.subtree_members(nd):
+                assert lb <= oracle.dist2(q, X[i]) * (1 + 1e-12)
