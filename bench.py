@@ -490,6 +490,100 @@ def tune_graph(args):
                           autotune=tune_rows, graphs=graph_rows)), flush=True)
 
 
+def tree_compare(args):
+    """Row f3 measured: pruning with the tree's internal-node synopses
+    (HK_Q_TREE) against the flat pass over all leaves, on a collection with
+    >= 1e5 leaves (N random walks x 256, leaf capacity args.tree_leaf, float16
+    copy), 2,000 hard queries (sigma 0.5 / 1.0) and 2,000 easy ones (sigma
+    0.01 / 0.1), k = 10, through the precision form and the float32 path.
+    Prints one JSON line."""
+    import torch
+    from paper_2212_13297_gb300 import binding, workload
+    import __graft_entry__
+    __graft_entry__.build()
+    N, n, tau, k, B = args.tree_n, 256, args.tree_leaf, 10, 2000
+    X = workload.random_walk(N, n, seed=0, device="cuda")
+    t0 = time.perf_counter()
+    idx = binding.Index(X, tau, flags=binding.HK_BUILD_FP16)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    batches = {"hard": workload.queries(X, B, [0.5, 1.0], seed=1)[0],
+               "easy": workload.queries(X, B, [0.01, 0.1], seed=3)[0]}
+    del X
+    torch.cuda.empty_cache()
+    info = idx.info()
+    rows = []
+    for name, Q in batches.items():
+        for form, f in (("precision", binding.HK_Q_BF16), ("float32", 0)):
+            if form == "float32" and name == "hard":
+                continue   # minutes per batch at this size; the precision form shows the same pruning
+            for mode, tf in (("flat", 0), ("tree", binding.HK_Q_TREE)):
+                for _ in range(max(1, args.warmup)):
+                    idx.query(Q, k, flags=f | tf)
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                agg = {}
+                for _ in range(args.steps):
+                    _, _, st = idx.query(Q, k, flags=f | tf)
+                    for key, v in st.items():
+                        agg[key] = agg.get(key, 0) + v
+                ev1.record()
+                torch.cuda.synchronize()
+                t = ev0.elapsed_time(ev1) / 1e3
+                rows.append(dict(queries=name, form=form, mode=mode, queries_per_s=B * args.steps / t,
+                                 ms_per_batch=t / args.steps * 1e3,
+                                 lb_evaluations_per_query=agg["lb_evaluations"] / agg["queries"],
+                                 leaves_candidate_per_query=agg["leaves_candidate"] / agg["queries"]))
+    print(json.dumps(dict(metric="row f3: flat LB_EAPCA over every leaf vs tree pruning (HK_Q_TREE), exact 10-NN",
+                          unit="queries/s", data="synthetic",
+                          config=dict(workload="%d random walks x %d, leaf %d, float16 copy, 2000 queries per "
+                                               "batch (hard: sigma 0.5/1.0, easy: 0.01/0.1), k=%d" % (N, n, tau, k),
+                                      leaves=info["leaves"], depth=info["depth"], build_s=build_s),
+                          rows=rows)), flush=True)
+
+
+def dtw_bench(args):
+    """Row f4 measured: exact k-NN under DTW (Sakoe-Chiba band) through the
+    index, 1M random walks x 256, leaf 1K, band 12 (about 5% of n), 100
+    queries (sigma 0.1 / 0.5), k = 10; the same batch under the Euclidean
+    distance for comparison.  Prints one JSON line."""
+    import torch
+    from paper_2212_13297_gb300 import binding, workload
+    import __graft_entry__
+    __graft_entry__.build()
+    N, n, tau, k, band, B = 1_000_000, 256, 1000, 10, 12, 100
+    X = workload.random_walk(N, n, seed=0, device="cuda")
+    Q, _ = workload.queries(X, B, [0.1, 0.5], seed=1)
+    idx = binding.Index(X, tau)
+    del X
+    torch.cuda.empty_cache()
+    out = {}
+    for name, call in (("dtw", lambda: idx.query_dtw(Q, k, band)), ("euclidean", lambda: idx.query(Q, k))):
+        for _ in range(max(1, args.warmup)):
+            call()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        agg = {}
+        for _ in range(args.steps):
+            _, _, st = call()
+            for key, v in st.items():
+                agg[key] = agg.get(key, 0) + v
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out[name] = dict(queries_per_s=B * args.steps / t, ms_per_batch=t / args.steps * 1e3,
+                         leaves_candidate_frac=agg["leaves_candidate"] / max(1, agg["leaves_total"]),
+                         series_candidate_per_query=agg["series_candidate"] / agg["queries"],
+                         word_bound_pruned_frac=agg["series_sax_pruned"] / max(1, agg["series_candidate"]),
+                         keogh_or_abandoned_frac=agg["series_abandoned"] / max(1, agg["series_candidate"]),
+                         full_per_query=agg["series_full"] / agg["queries"])
+    print(json.dumps(dict(metric="row f4: exact 10-NN under DTW (band %d) through the index" % band,
+                          unit="queries/s", data="synthetic",
+                          config=dict(workload="1M random walks x 256, leaf 1K, 100 queries (sigma 0.1/0.5), "
+                                               "k=10, band 12"),
+                          results=out)), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -523,6 +617,12 @@ def main():
     ap.add_argument("--tune-graph", action="store_true",
                     help="instead of the step benchmark, hk_tune's choice against the defaults and "
                          "CUDA-graph replay against ordinary calls (10M x 256)")
+    ap.add_argument("--tree", action="store_true",
+                    help="instead of the step benchmark, flat vs tree pruning (HK_Q_TREE) on >= 1e5 leaves")
+    ap.add_argument("--tree-n", type=int, default=100_000_000)
+    ap.add_argument("--tree-leaf", type=int, default=1000)
+    ap.add_argument("--dtw", action="store_true",
+                    help="instead of the step benchmark, exact k-NN under DTW through the index")
     ap.add_argument("--serve-mix", type=float, default=0.0,
                     help="instead of the step benchmark, serve the four-collection mix at this "
                          "rate (requests/s) and print its latency line")
@@ -542,6 +642,12 @@ def main():
         return
     if args.tune_graph:
         tune_graph(args)
+        return
+    if args.tree:
+        tree_compare(args)
+        return
+    if args.dtw:
+        dtw_bench(args)
         return
 
     import numpy as np

@@ -97,10 +97,11 @@ int hk_index_info_get(const hk_index *idx, hk_index_info *out);
 
 /*
  * hk_save -- write the index to the file at path (created or truncated): the
- * tree's leaf synopses and segmentations, the leaf-ordered raw series, their
- * positions' original ids and iSAX words, and the 16-bit copy when the index
- * has one -- the paper's HTree, LRDFile and LSDFile (Sec. 3.3) in one file.
- * Layout: the tag "HKIDX001", a header of sizes, then each array as a 64-bit
+ * tree (links, position ranges, segmentations and synopses of its leaves and
+ * internal nodes), the leaf-ordered raw series, their positions' original
+ * ids and iSAX words, and the 16-bit copy when the index has one -- the
+ * paper's HTree, LRDFile and LSDFile (Sec. 3.3) in one file.
+ * Layout: the tag "HKIDX002", a header of sizes, then each array as a 64-bit
  * byte count followed by its bytes, then an FNV-1a 64-bit checksum of all
  * array bytes; integers and floats in this machine's byte order.  Returns
  * HK_EIO if the file cannot be written.  The index is not modified.
@@ -132,6 +133,14 @@ int hk_load(const char *path, void *stream, hk_index **out);
                               space and replay it (same answers).  The index
                               holds one graph; calls on one index must not run
                               concurrently.  HK_Q_TIMING is ignored.          */
+#define HK_Q_TREE 64u      /* prune with the tree's internal-node synopses
+                              (Sec. 3.3): the approximate search walks the
+                              tree best-first by LB_EAPCA (Approx-kNN), and
+                              candidate leaves come from a top-down pass that
+                              evaluates a node only where its parent stayed,
+                              pruning whole subtrees (same answers; fewer
+                              LB_EAPCA evaluations when leaves are many).
+                              Not with HK_Q_NOPRUNE.                          */
 
 typedef struct {
     int32_t l_max;        /* leaves visited by the approximate search per query
@@ -175,6 +184,9 @@ typedef struct {
     int64_t tc_leaf_bytes;        /* 16-bit rows and norms of the leaves the exact
                                      step scans, each leaf once: the least DRAM
                                      traffic that step can have                  */
+    int64_t lb_evaluations;       /* (query, node) LB_EAPCA evaluations: queries x
+                                     leaves without HK_Q_TREE, the nodes visited
+                                     with it                                     */
 } hk_query_stats;
 
 /*
@@ -205,6 +217,26 @@ int hk_query_opts_default(hk_query_opts *out);
 int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k,
              const hk_query_opts *opts, void *stream, int64_t *out_ids,
              float *out_dist, hk_query_stats *stats);
+
+/*
+ * hk_query_dtw -- exact k-NN under Dynamic Time Warping (Sec. 2: Hercules
+ * supports any distance with a lower-bounding distance, e.g. DTW with the
+ * bound of Keogh and Ratanamahatana, KAIS 2005), on the same index.
+ * Distance: squared point costs summed along the cheapest warping path that
+ * stays within the Sakoe-Chiba band |i - j| <= band (0 <= band <=
+ * min(16, n-1); band 0 is the squared Euclidean distance):
+ *   D(i,j) = (q_i - x_j)^2 + min(D(i-1,j-1), D(i-1,j), D(i,j-1)).
+ * Pruning: the query's envelope against each leaf synopsis (segment means),
+ * against each series' iSAX word, and LB_Keogh against its raw points, then
+ * the DTW with early abandoning; all in float32 with certified rounding,
+ * candidates rescored in binary64.  Outputs as hk_query: ids ascending by
+ * (binary64 DTW, id), out_dist = sqrt(DTW).  opts: l_max and HK_Q_NOSAX are
+ * used, other fields ignored; NULL = defaults.  Calls on one index must not
+ * run concurrently (they share its DTW work space).
+ */
+int hk_query_dtw(hk_index *idx, const float *Q, int32_t nq, int32_t k, int32_t band,
+                 const hk_query_opts *opts, void *stream, int64_t *out_ids, float *out_dist,
+                 hk_query_stats *stats);
 
 /*
  * hk_scan_knn -- exact k-NN by scanning every series of a collection (no
@@ -348,6 +380,22 @@ int hk_isax_breakpoints(float out[255]);
 int hk_index_export(const hk_index *idx, int64_t *perm, int64_t *leaf_off,
                     int32_t *leaf_nseg, int32_t *seg_end, double *env,
                     uint8_t *sax);
+
+/*
+ * hk_index_export_tree -- copy the whole tree (HTree, Sec. 3.3) to host
+ * buffers (any may be NULL), for T = 2L - 1 nodes: leaves 0..L-1 in leaf
+ * order, internal nodes L..T-1 with parents before children:
+ *   parent[T], left[T], right[T]   node ids (-1: none)
+ *   beg[T], end[T]                 the leaf-order positions of the node's
+ *                                  series: [beg, end)
+ *   nseg[T], seg_end[T*64]         segmentation (row of 64 per node)
+ *   env[T*64*4]                    synopsis per segment (mu_min, mu_max,
+ *                                  sd_min, sd_max) over every series that
+ *                                  traversed the node (Sec. 3.3), binary64
+ */
+int hk_index_export_tree(const hk_index *idx, int32_t *parent, int32_t *left, int32_t *right,
+                         int64_t *beg, int64_t *end, int32_t *nseg, int32_t *seg_end,
+                         double *env);
 
 /*
  * hk_debug_lb_eapca -- LB_EAPCA (squared, binary64) of each query to each

@@ -15,6 +15,13 @@ it.  Each function cites the passage it follows:
   isax_breakpoints         Sec. 2: alphabet 256, standard normal quantiles
   isax_symbol, isax_word   Sec. 2: iSAX symbols of PAA values
   lb_sax                   Sec. 3.4 (CSWorker, CRWorker): LB_SAX
+  dtw2, dtw_knn, DtwKnnStream  Sec. 2: DTW (squared point costs, Sakoe-Chiba
+                           band) as a distance with a lower bound, and k-NN
+                           under it
+  envelope, lb_keogh, lb_keogh_eapca, lb_keogh_sax
+                           LB_Keogh (Keogh & Ratanamahatana 2005, the bound
+                           the paper cites for DTW) and its forms against a
+                           node synopsis and an iSAX word
   tree.build_tree          Sec. 3.2 and Algorithm InsertSeriesToNode (Sec. 3.3):
                            sequential insertion with H/V node splits; the split
                            policy, which the paper leaves to DSTree, is the
@@ -69,6 +76,20 @@ def _lib():
         L.hko_isax_symbol.argtypes = [ctypes.c_double, f32p]
         L.hko_lb_sax.restype = ctypes.c_double
         L.hko_lb_sax.argtypes = [f64p, u8p, ctypes.c_int, ctypes.c_int, f32p]
+        L.hko_dtw2.restype = ctypes.c_double
+        L.hko_dtw2.argtypes = [f32p, f32p, ctypes.c_int, ctypes.c_int]
+        L.hko_dtw_knn_update.restype = ctypes.c_int
+        L.hko_dtw_knn_update.argtypes = [f32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, f32p,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p, f64p,
+                                         ctypes.c_int]
+        L.hko_envelope.restype = None
+        L.hko_envelope.argtypes = [f32p, ctypes.c_int, ctypes.c_int, f32p, f32p]
+        L.hko_lb_keogh.restype = ctypes.c_double
+        L.hko_lb_keogh.argtypes = [f32p, f32p, ctypes.c_int, ctypes.c_int]
+        L.hko_lb_keogh_eapca.restype = ctypes.c_double
+        L.hko_lb_keogh_eapca.argtypes = [f32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, f64p]
+        L.hko_lb_keogh_sax.restype = ctypes.c_double
+        L.hko_lb_keogh_sax.argtypes = [f32p, ctypes.c_int, ctypes.c_int, u8p, f32p]
         _LIB = L
     return _LIB
 
@@ -217,3 +238,77 @@ def exact_answer(X, Q, k: int, nthreads: int | None = None):
     the reported Euclidean distances sqrt(D) rounded to float32."""
     ids, d2 = knn(X, Q, k, nthreads)
     return ids, np.sqrt(d2).astype(np.float32), d2
+
+
+# ---- DTW with a Sakoe-Chiba band (Sec. 2: any distance with a lower bound)
+
+def dtw2(q, x, band: int) -> float:
+    """DTW with squared point costs and a Sakoe-Chiba band of half-width
+    `band`, binary64 (the dynamic programme in hk_oracle.c)."""
+    q = _f32(q)
+    x = _f32(x)
+    assert q.shape == x.shape and q.ndim == 1 and band >= 0
+    return _lib().hko_dtw2(_p(q, ctypes.c_float), _p(x, ctypes.c_float), q.size, int(band))
+
+
+class DtwKnnStream(KnnStream):
+    """Brute-force k-NN under DTW(band), fed block by block like KnnStream."""
+
+    def __init__(self, Q, k: int, band: int, nthreads: int | None = None):
+        super().__init__(Q, k, nthreads)
+        self.band = int(band)
+
+    def update(self, Xblock, id0: int | None = None):
+        X = _f32(Xblock)
+        assert X.ndim == 2 and X.shape[1] == self.n
+        if id0 is None:
+            id0 = self.next_id
+        rc = _lib().hko_dtw_knn_update(_p(X, ctypes.c_float), int(id0), X.shape[0], self.n,
+                                       _p(self.Q, ctypes.c_float), self.nq, self.k, self.band,
+                                       _p(self.ids, ctypes.c_int64), _p(self.d2, ctypes.c_double),
+                                       self.nthreads)
+        if rc != 0:
+            raise RuntimeError("hko_dtw_knn_update failed: %d" % rc)
+        self.next_id = int(id0) + X.shape[0]
+
+
+def dtw_knn(X, Q, k: int, band: int, nthreads: int | None = None):
+    """Exact k-NN under DTW(band): (ids, squared DTW values), ascending (D, id)."""
+    s = DtwKnnStream(Q, k, band, nthreads)
+    s.update(X, 0)
+    return s.result()
+
+
+def envelope(q, band: int):
+    """(L, U): min and max of q over each window j-band .. j+band."""
+    q = _f32(q)
+    L = np.empty_like(q)
+    U = np.empty_like(q)
+    _lib().hko_envelope(_p(q, ctypes.c_float), q.size, int(band), _p(L, ctypes.c_float),
+                        _p(U, ctypes.c_float))
+    return L, U
+
+
+def lb_keogh(q, x, band: int) -> float:
+    """LB_Keogh^2(q, x) for DTW(band)."""
+    q = _f32(q)
+    x = _f32(x)
+    return _lib().hko_lb_keogh(_p(q, ctypes.c_float), _p(x, ctypes.c_float), q.size, int(band))
+
+
+def lb_keogh_eapca(q, band: int, seg_end, env) -> float:
+    """LB_Keogh of q against a node synopsis env[m][4] over seg_end."""
+    q = _f32(q)
+    se = np.ascontiguousarray(seg_end, dtype=np.int32)
+    env = np.ascontiguousarray(env, dtype=np.float64).reshape(-1)
+    return _lib().hko_lb_keogh_eapca(_p(q, ctypes.c_float), q.size, int(band), se.size,
+                                     _p(se, ctypes.c_int32), _p(env, ctypes.c_double))
+
+
+def lb_keogh_sax(q, band: int, sym, bp32) -> float:
+    """LB_Keogh of q against an iSAX word (16 symbols)."""
+    q = _f32(q)
+    sym = np.ascontiguousarray(sym, dtype=np.uint8)
+    bp32 = _f32(bp32)
+    return _lib().hko_lb_keogh_sax(_p(q, ctypes.c_float), q.size, int(band), _p(sym, ctypes.c_uint8),
+                                   _p(bp32, ctypes.c_float))

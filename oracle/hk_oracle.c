@@ -25,6 +25,12 @@
  *   hko_isax_symbol  iSAX symbol of a PAA value (alphabet 256, Sec. 2)
  *   hko_lb_sax       LB_SAX of a query PAA to an iSAX word (Sec. 3.4,
  *                    Algorithms CSWorker and CRWorker)
+ *   hko_dtw2         DTW with a Sakoe-Chiba band (Sec. 2: any distance with
+ *                    a lower bound, e.g. DTW), squared point costs
+ *   hko_dtw_knn_update  brute-force k-NN under that DTW
+ *   hko_envelope, hko_lb_keogh, hko_lb_keogh_eapca, hko_lb_keogh_sax
+ *                    LB_Keogh (the lower bound the paper cites for DTW) and
+ *                    its forms against a node synopsis and an iSAX word
  *
  * Parity pins for every function live in tests/test_oracle_*.py.
  */
@@ -72,12 +78,15 @@ static void topk_insert(double *ds, int64_t *ids, int k, double d, int64_t id)
     ids[p] = id;
 }
 
+double hko_dtw2(const float *q, const float *x, int n, int r);
+
 typedef struct {
     const float *X;
     int64_t id0, cnt;
     int n;
     const float *Q;
     int k;
+    int band;        /* < 0: Euclidean; >= 0: DTW with this band */
     int64_t *ids;
     double *d2;
     int q_begin, q_end;
@@ -91,7 +100,8 @@ static void *knn_worker(void *arg)
         double *ds = J->d2 + (int64_t)qi * J->k;
         int64_t *is = J->ids + (int64_t)qi * J->k;
         for (int64_t r = 0; r < J->cnt; ++r) {
-            double d = hko_dist2(q, J->X + r * J->n, J->n);
+            double d = J->band < 0 ? hko_dist2(q, J->X + r * J->n, J->n)
+                                   : hko_dtw2(q, J->X + r * J->n, J->n, J->band);
             topk_insert(ds, is, J->k, d, J->id0 + r);
         }
     }
@@ -113,9 +123,27 @@ void hko_knn_init(int nq, int k, int64_t *ids, double *d2)
  * over consecutive blocks of a collection gives the same lists as one call
  * over the whole collection: every series is offered to every query's list,
  * in id order.  Queries are divided among nthreads threads. */
+static int knn_run(const float *X, int64_t id0, int64_t cnt, int n, const float *Q, int nq, int k,
+                   int band, int64_t *ids, double *d2, int nthreads);
+
 int hko_knn_update(const float *X, int64_t id0, int64_t cnt, int n,
                    const float *Q, int nq, int k, int64_t *ids, double *d2,
                    int nthreads)
+{
+    return knn_run(X, id0, cnt, n, Q, nq, k, -1, ids, d2, nthreads);
+}
+
+/* The same under DTW with a Sakoe-Chiba band of half-width band >= 0. */
+int hko_dtw_knn_update(const float *X, int64_t id0, int64_t cnt, int n,
+                       const float *Q, int nq, int k, int band, int64_t *ids,
+                       double *d2, int nthreads)
+{
+    if (band < 0) return -1;
+    return knn_run(X, id0, cnt, n, Q, nq, k, band, ids, d2, nthreads);
+}
+
+static int knn_run(const float *X, int64_t id0, int64_t cnt, int n, const float *Q, int nq, int k,
+                   int band, int64_t *ids, double *d2, int nthreads)
 {
     if (n <= 0 || nq < 0 || k <= 0 || cnt < 0) return -1;
     if (nthreads < 1) nthreads = 1;
@@ -125,7 +153,7 @@ int hko_knn_update(const float *X, int64_t id0, int64_t cnt, int n,
     if (!jobs || !th) { free(jobs); free(th); return -2; }
     for (int t = 0; t < nthreads; ++t) {
         knn_job *J = &jobs[t];
-        J->X = X; J->id0 = id0; J->cnt = cnt; J->n = n; J->Q = Q; J->k = k;
+        J->X = X; J->id0 = id0; J->cnt = cnt; J->n = n; J->Q = Q; J->k = k; J->band = band;
         J->ids = ids; J->d2 = d2;
         J->q_begin = (int)((int64_t)nq * t / nthreads);
         J->q_end = (int)((int64_t)nq * (t + 1) / nthreads);
@@ -286,4 +314,150 @@ double hko_lb_sax(const double *paa_q, const uint8_t *sym, int w, int n,
         acc = acc + d * d;
     }
     return ((double)n / (double)w) * acc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* DTW (Sec. 2: Hercules supports any distance with a lower-bounding          */
+/* distance, e.g. DTW, with the lower bound of Keogh and Ratanamahatana,     */
+/* KAIS 2005).  Squared point costs, a Sakoe-Chiba band of half-width r:     */
+/*   D(i, j) = (q_i - x_j)^2 + min(D(i-1, j-1), D(i-1, j), D(i, j-1))        */
+/* over |i - j| <= r, with D = +inf outside the band and D(-1,-1) = 0; the   */
+/* distance is D(n-1, n-1).  Rows i ascending, columns j ascending; the     */
+/* minimum is exact, the cost and the addition are rounded once each.        */
+/* With r = 0 the only path is the diagonal and D equals hko_dist2.          */
+/* ------------------------------------------------------------------------ */
+double hko_dtw2(const float *q, const float *x, int n, int r)
+{
+    double *prev = (double *)malloc(sizeof(double) * (size_t)n);
+    double *cur = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!prev || !cur) { free(prev); free(cur); return NAN; }
+    for (int j = 0; j < n; ++j) prev[j] = INFINITY;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) cur[j] = INFINITY;
+        int jlo = i - r < 0 ? 0 : i - r;
+        int jhi = i + r > n - 1 ? n - 1 : i + r;
+        for (int j = jlo; j <= jhi; ++j) {
+            double best;
+            if (i == 0 && j == 0) {
+                best = 0.0;
+            } else {
+                double a = (i > 0 && j > 0) ? prev[j - 1] : INFINITY;
+                double b = i > 0 ? prev[j] : INFINITY;
+                double c = j > 0 ? cur[j - 1] : INFINITY;
+                best = a < b ? a : b;
+                best = c < best ? c : best;
+            }
+            double d = (double)q[i] - (double)x[j];
+            double t = d * d;
+            cur[j] = t + best;
+        }
+        double *sw = prev; prev = cur; cur = sw;
+    }
+    double out = prev[n - 1];
+    free(prev);
+    free(cur);
+    return out;
+}
+
+/* Envelope of q for band r (Keogh 2005): L_j = min, U_j = max of q over
+ * positions j-r .. j+r inside [0, n). */
+void hko_envelope(const float *q, int n, int r, float *L, float *U)
+{
+    for (int j = 0; j < n; ++j) {
+        int a = j - r < 0 ? 0 : j - r;
+        int b = j + r > n - 1 ? n - 1 : j + r;
+        float lo = q[a], hi = q[a];
+        for (int t = a + 1; t <= b; ++t) {
+            if (q[t] < lo) lo = q[t];
+            if (q[t] > hi) hi = q[t];
+        }
+        L[j] = lo;
+        U[j] = hi;
+    }
+}
+
+/* LB_Keogh^2(q, x) = sum_j dist(x_j, [L_j, U_j])^2, index order: every
+ * warping path matches x_j to some q_i with |i - j| <= r, which lies in
+ * [L_j, U_j], so each term is at most that path's cost at x_j. */
+double hko_lb_keogh(const float *q, const float *x, int n, int r)
+{
+    float *L = (float *)malloc(sizeof(float) * (size_t)n);
+    float *U = (float *)malloc(sizeof(float) * (size_t)n);
+    if (!L || !U) { free(L); free(U); return NAN; }
+    hko_envelope(q, n, r, L, U);
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double d = dist_to_range((double)x[j], (double)L[j], (double)U[j]);
+        s = s + d * d;
+    }
+    free(L);
+    free(U);
+    return s;
+}
+
+/* Distance between the closed intervals [a1, b1] and [a2, b2]. */
+static double interval_gap(double a1, double b1, double a2, double b2)
+{
+    if (a1 > b2) return a1 - b2;
+    if (a2 > b1) return a2 - b1;
+    return 0.0;
+}
+
+/* Mean of v[a..b), binary64, sequential. */
+static double mean_f(const float *v, int a, int b)
+{
+    double s = 0.0;
+    for (int j = a; j < b; ++j) s = s + (double)v[j];
+    return s / (double)(b - a);
+}
+
+/* LB_Keogh against a node synopsis (a reading: the paper gives no formula).
+ * dist(x_j, [L_j, U_j])^2 is jointly convex in (x_j, L_j, U_j), so over a
+ * segment of l points its sum is at least l times its value at the means
+ * (Jensen): l dist(mean x, [mean L, mean U])^2, and with the node's series'
+ * segment means in [mu_min, mu_max] at least
+ * l gap([mu_min, mu_max], [mean L, mean U])^2.  Segments in order. */
+double hko_lb_keogh_eapca(const float *q, int n, int r, int m, const int32_t *seg_end, const double *env)
+{
+    float *L = (float *)malloc(sizeof(float) * (size_t)n);
+    float *U = (float *)malloc(sizeof(float) * (size_t)n);
+    if (!L || !U) { free(L); free(U); return NAN; }
+    hko_envelope(q, n, r, L, U);
+    double acc = 0.0;
+    int a = 0;
+    for (int i = 0; i < m; ++i) {
+        int b = seg_end[i];
+        double lm = mean_f(L, a, b), um = mean_f(U, a, b);
+        double g = interval_gap(env[4 * i], env[4 * i + 1], lm, um);
+        double l = (double)(b - a);
+        acc = acc + l * (g * g);
+        a = b;
+    }
+    free(L);
+    free(U);
+    return acc;
+}
+
+/* LB_Keogh against an iSAX word: the same argument over the 16 PAA segments,
+ * with the series' PAA inside its symbol's cell [beta_s, beta_{s+1}):
+ * (n/16) sum_i gap(cell_i, [PAA(L)_i, PAA(U)_i])^2. */
+double hko_lb_keogh_sax(const float *q, int n, int r, const uint8_t *sym, const float *bp /* 255 */)
+{
+    float *L = (float *)malloc(sizeof(float) * (size_t)n);
+    float *U = (float *)malloc(sizeof(float) * (size_t)n);
+    if (!L || !U) { free(L); free(U); return NAN; }
+    hko_envelope(q, n, r, L, U);
+    int w = 16, l = n / w;
+    double acc = 0.0;
+    for (int i = 0; i < w; ++i) {
+        double lm = mean_f(L, i * l, (i + 1) * l), um = mean_f(U, i * l, (i + 1) * l);
+        int s = sym[i];
+        double lo = s == 0 ? -INFINITY : (double)bp[s - 1];
+        double hi = s == 255 ? INFINITY : (double)bp[s];
+        double g = interval_gap(lo, hi, lm, um);
+        acc = acc + g * g;
+    }
+    free(L);
+    free(U);
+    return (double)l * acc;
 }

@@ -33,6 +33,7 @@ HK_Q_NOPRUNE = 4
 HK_Q_TIMING = 8
 HK_Q_BF16 = 16
 HK_Q_GRAPH = 32
+HK_Q_TREE = 64
 
 
 class hk_build_opts(ctypes.Structure):
@@ -52,7 +53,7 @@ class hk_query_stats(ctypes.Structure):
         "series_sax_pruned", "series_abandoned", "series_full", "points_computed", "rescored",
         "fallback_queries", "retried_queries", "work_items", "skip_sequential", "scan_ns", "kernel_launches",
         "scan_bytes", "tc_pairs", "tc_candidates", "tc_ns", "tc_bytes", "tc_approx_pairs",
-        "tc_approx_ns", "tc_approx_bytes", "tc_leaf_bytes")]
+        "tc_approx_ns", "tc_approx_bytes", "tc_leaf_bytes", "lb_evaluations")]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -91,9 +92,10 @@ class HerculesError(RuntimeError):
 _lib = None
 
 # every symbol include/hercules_gb300.h declares
-EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_scan_knn",
+EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_query_dtw", "hk_scan_knn",
            "hk_scan_knn_noalloc",
-           "hk_isax_breakpoints", "hk_index_export", "hk_debug_lb_eapca", "hk_debug_lb_sax",
+           "hk_isax_breakpoints", "hk_index_export", "hk_index_export_tree", "hk_debug_lb_eapca",
+           "hk_debug_lb_sax",
            "hk_debug_tc_dist", "hk_server_create", "hk_server_add", "hk_submit", "hk_poll",
            "hk_server_stats_get", "hk_server_destroy", "hk_tune", "hk_save", "hk_load",
            "hk_query_opts_default", "hk_debug_device_allocs", "hk_debug_fail_device_alloc",
@@ -117,12 +119,15 @@ def lib():
         L.hk_query.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32,
                                ctypes.POINTER(hk_query_opts), vp, vp, vp,
                                ctypes.POINTER(hk_query_stats)]
+        L.hk_query_dtw.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.POINTER(hk_query_opts), vp, vp, vp, ctypes.POINTER(hk_query_stats)]
         L.hk_scan_knn.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, ctypes.c_int32,
                                   ctypes.c_int32, vp, vp, vp]
         L.hk_scan_knn_noalloc.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, ctypes.c_int32,
                                           ctypes.c_int32, vp, vp, vp]
         L.hk_isax_breakpoints.argtypes = [vp]
         L.hk_index_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.hk_index_export_tree.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.hk_debug_lb_eapca.argtypes = [vp, vp, ctypes.c_int32, vp]
         L.hk_debug_lb_sax.argtypes = [vp, vp, ctypes.c_int32, vp]
         L.hk_debug_tc_dist.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
@@ -269,6 +274,22 @@ class Index:
                               _ptr(ids), _ptr(dist), ctypes.byref(st)))
         return ids, dist, st.as_dict()
 
+    def query_dtw(self, Q, k: int, band: int, l_max=0, flags=0, stream=None, out=None):
+        """Exact k-NN under DTW with a Sakoe-Chiba band: (ids, dist, stats)
+        as query()."""
+        nq = Q.shape[0]
+        assert Q.shape[1] == self.n
+        if out is None:
+            ids = _out_like(Q, (nq, k), np.int64, _torch_dtype("int64"))
+            dist = _out_like(Q, (nq, k), np.float32, _torch_dtype("float32"))
+        else:
+            ids, dist = out
+        o = hk_query_opts(int(l_max), -1.0, -1.0, int(flags), 0, 0)
+        st = hk_query_stats()
+        _check(lib().hk_query_dtw(self._h, _ptr(Q), nq, int(k), int(band), ctypes.byref(o), _stream(stream),
+                                  _ptr(ids), _ptr(dist), ctypes.byref(st)))
+        return ids, dist, st.as_dict()
+
     def tune(self, Q, k: int, keep_flags=0, stream=None):
         """hk_tune: the fastest query configuration on the sample batch Q, as a
         dict of hk_query keyword arguments plus ms_per_query / tried /
@@ -294,6 +315,17 @@ class Index:
         _check(lib().hk_index_export(self._h, _ptr(perm), _ptr(leaf_off), _ptr(nseg),
                                      _ptr(seg_end), _ptr(env), _ptr(sax)))
         return dict(perm=perm, leaf_off=leaf_off, nseg=nseg, seg_end=seg_end, env=env, sax=sax)
+
+    def export_tree(self):
+        """The whole tree as numpy arrays (see hk_index_export_tree)."""
+        T = 2 * self.info()["leaves"] - 1
+        out = dict(parent=np.empty(T, np.int32), left=np.empty(T, np.int32), right=np.empty(T, np.int32),
+                   beg=np.empty(T, np.int64), end=np.empty(T, np.int64), nseg=np.empty(T, np.int32),
+                   seg_end=np.empty((T, 64), np.int32), env=np.empty((T, 64, 4), np.float64))
+        _check(lib().hk_index_export_tree(self._h, *[_ptr(out[k]) for k in
+                                                     ("parent", "left", "right", "beg", "end", "nseg",
+                                                      "seg_end", "env")]))
+        return out
 
     def debug_lb_eapca(self, Q):
         L = self.info()["leaves"]

@@ -198,6 +198,8 @@ int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k, const hk_quer
                 hk::fail(HK_EINVAL, "HK_Q_BF16 takes series of length <= %d (n=%d)", hk::kTcMaxLen, idx->n);
             if (o.flags & HK_Q_NOPRUNE) hk::fail(HK_EINVAL, "HK_Q_BF16 and HK_Q_NOPRUNE exclude each other");
         }
+        if ((o.flags & HK_Q_TREE) && (o.flags & HK_Q_NOPRUNE))
+            hk::fail(HK_EINVAL, "HK_Q_TREE and HK_Q_NOPRUNE exclude each other");
         cudaStream_t s = (cudaStream_t)stream;
         idx->stream = s;
         // host queries go through the index's staging buffer: no device
@@ -211,6 +213,37 @@ int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k, const hk_quer
         }
         hk::check_finite(Qd, (int64_t)nq * idx->n, s, "Q");
         hk::run_query(idx, Qd, nq, k, o, s, out_ids, out_dist, stats);
+    });
+}
+
+int hk_query_dtw(hk_index *idx, const float *Q, int32_t nq, int32_t k, int32_t band,
+                 const hk_query_opts *opts, void *stream, int64_t *out_ids, float *out_dist,
+                 hk_query_stats *stats) {
+    return guard([&] {
+        if (!idx || !Q || !out_ids || !out_dist) hk::fail(HK_EINVAL, "NULL argument");
+        if (nq < 1) hk::fail(HK_EINVAL, "nq=%d must be >= 1", nq);
+        if (k < 1 || k > HK_MAX_K || (int64_t)k > idx->N)
+            hk::fail(HK_EINVAL, "k=%d must be in [1, min(N=%lld, %d)]", k, (long long)idx->N, HK_MAX_K);
+        if (band < 0 || band > hk::kDtwMaxBand || band >= idx->n)
+            hk::fail(HK_EINVAL, "band=%d must be in [0, min(%d, n-1)]", band, hk::kDtwMaxBand);
+        hk_query_opts o;
+        if (opts) {
+            o = *opts;
+        } else {
+            std::memset(&o, 0, sizeof(o));
+        }
+        if (o.l_max < 0) hk::fail(HK_EINVAL, "l_max=%d must be >= 0", o.l_max);
+        cudaStream_t s = (cudaStream_t)stream;
+        idx->stream = s;
+        const float *Qd = Q;
+        if (!hk::is_device_ptr(Q)) {
+            const size_t count = (size_t)nq * idx->n;
+            idx->qstage.reserve(count, s);
+            HK_CHECK_CUDA(cudaMemcpyAsync(idx->qstage.p, Q, count * sizeof(float), cudaMemcpyHostToDevice, s));
+            Qd = idx->qstage.p;
+        }
+        hk::check_finite(Qd, (int64_t)nq * idx->n, s, "Q");
+        hk::run_query_dtw(idx, Qd, nq, k, band, o, s, out_ids, out_dist, stats);
     });
 }
 
@@ -247,6 +280,33 @@ int hk_index_export(const hk_index *idx, int64_t *perm, int64_t *leaf_off, int32
                                      cudaMemcpyDeviceToHost));
         if (sax)
             HK_CHECK_CUDA(cudaMemcpy(sax, idx->sax.p, N * hk::kWord, cudaMemcpyDeviceToHost));
+    });
+}
+
+int hk_index_export_tree(const hk_index *idx, int32_t *parent, int32_t *left, int32_t *right,
+                         int64_t *beg, int64_t *end, int32_t *nseg, int32_t *seg_end, double *env) {
+    return guard([&] {
+        if (!idx) hk::fail(HK_EINVAL, "idx is NULL");
+        const int64_t L = idx->L, T = idx->T, I = T - L;
+        if (parent) std::memcpy(parent, idx->h_tree_parent.data(), T * sizeof(int32_t));
+        if (left) std::memcpy(left, idx->h_tree_left.data(), T * sizeof(int32_t));
+        if (right) std::memcpy(right, idx->h_tree_right.data(), T * sizeof(int32_t));
+        if (beg) std::memcpy(beg, idx->h_tree_beg.data(), T * sizeof(int64_t));
+        if (end) std::memcpy(end, idx->h_tree_end.data(), T * sizeof(int64_t));
+        if (nseg) {
+            std::memcpy(nseg, idx->h_leaf_nseg.data(), L * sizeof(int32_t));
+            std::memcpy(nseg + L, idx->h_inode_nseg.data(), I * sizeof(int32_t));
+        }
+        if (seg_end) {
+            std::memcpy(seg_end, idx->h_seg_end.data(), L * hk::kMaxSeg * sizeof(int32_t));
+            std::memcpy(seg_end + L * hk::kMaxSeg, idx->h_inode_seg_end.data(), I * hk::kMaxSeg * sizeof(int32_t));
+        }
+        if (env) {
+            HK_CHECK_CUDA(cudaMemcpy(env, idx->env.p, L * hk::kMaxSeg * 4 * sizeof(double), cudaMemcpyDeviceToHost));
+            if (I > 0)
+                HK_CHECK_CUDA(cudaMemcpy(env + L * hk::kMaxSeg * 4, idx->ienv.p, I * hk::kMaxSeg * 4 * sizeof(double),
+                                         cudaMemcpyDeviceToHost));
+        }
     });
 }
 

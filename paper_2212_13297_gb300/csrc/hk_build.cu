@@ -303,16 +303,21 @@ __global__ void k_gather_rows(const float *__restrict__ X, int n, const int32_t 
     }
 }
 
-// Leaf synopsis (Sec. 3.2): per segment, min/max of mean and std over the
-// leaf's series.  Block per leaf.
+// Node synopsis (Sec. 3.2-3.3): per segment of the node's segmentation,
+// min/max of mean and std over the series at positions [beg, end) -- a leaf's
+// own series, or for an internal node every series that traversed it (a
+// node's series occupy a contiguous run of leaf-order positions).  This is
+// what the paper's ProcessLeaf / VSplitSynopsis / HSplitSynopsis fold
+// arrives at.  Block per node.
 __global__ void __launch_bounds__(256) k_envelope(const float *__restrict__ Y, int n,
-                                                  const int64_t *__restrict__ leaf_off,
+                                                  const int64_t *__restrict__ beg,
+                                                  const int64_t *__restrict__ end,
                                                   const int32_t *__restrict__ leaf_nseg,
                                                   const int32_t *__restrict__ seg_end,
                                                   double *__restrict__ env) {
     __shared__ double red[4][8];
     const int64_t leaf = blockIdx.x;
-    const int64_t o = leaf_off[leaf], e = leaf_off[leaf + 1];
+    const int64_t o = beg[leaf], e = end[leaf];
     const int m = leaf_nseg[leaf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int a = 0;
@@ -374,6 +379,15 @@ struct HostNode {
     int64_t off, cnt;
     std::vector<int32_t> seg_end;
     bool unsplittable = false;
+    int32_t tid = 0;          // its record in the tree
+};
+
+// Every node the build creates (the tree the paper writes as HTree).
+struct TreeRec {
+    int64_t off, cnt;         // its series: leaf-order positions [off, off + cnt)
+    std::vector<int32_t> seg_end;
+    int32_t parent = -1, left = -1, right = -1;
+    int32_t level = 0;
 };
 
 unsigned grid_for(int64_t work, int per_block, int sms) {
@@ -385,6 +399,38 @@ unsigned grid_for(int64_t work, int per_block, int sms) {
 }
 
 }  // namespace
+
+void upload_tree(hk_index *idx, cudaStream_t s) {
+    const int64_t T = idx->T, L = idx->L, I = T - L;
+    // nodes by level
+    int maxl = 0;
+    for (int64_t u = 0; u < T; ++u) maxl = std::max(maxl, idx->h_tree_level[u]);
+    idx->h_level_off.assign(maxl + 2, 0);
+    for (int64_t u = 0; u < T; ++u) ++idx->h_level_off[idx->h_tree_level[u] + 1];
+    for (int d = 0; d <= maxl; ++d) idx->h_level_off[d + 1] += idx->h_level_off[d];
+    std::vector<int32_t> lv(T), fill(idx->h_level_off.begin(), idx->h_level_off.end() - 1);
+    for (int64_t u = 0; u < T; ++u) lv[fill[idx->h_tree_level[u]]++] = (int32_t)u;
+    auto up32 = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) {
+        d.alloc(h.size(), s);
+        if (!h.empty())
+            HK_CHECK_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    };
+    auto up64 = [&](DevBuf<int64_t> &d, const std::vector<int64_t> &h) {
+        d.alloc(h.size(), s);
+        if (!h.empty())
+            HK_CHECK_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    };
+    up32(idx->tree_parent, idx->h_tree_parent);
+    up32(idx->tree_left, idx->h_tree_left);
+    up32(idx->tree_right, idx->h_tree_right);
+    up64(idx->tree_beg, idx->h_tree_beg);
+    up64(idx->tree_end, idx->h_tree_end);
+    up32(idx->inode_nseg, idx->h_inode_nseg);
+    up32(idx->inode_seg, idx->h_inode_seg);
+    up32(idx->level_nodes, lv);
+    if (idx->ienv.n != (size_t)I * kMaxSeg * 4) idx->ienv.alloc((size_t)I * kMaxSeg * 4, s);
+    HK_CHECK_CUDA(cudaStreamSynchronize(s));   // the host vectors above go out of scope
+}
 
 void build_index(hk_index *idx, const float *Xsrc, int64_t N, int n, const hk_build_opts &o,
                  cudaStream_t s) {
@@ -408,12 +454,19 @@ void build_index(hk_index *idx, const float *Xsrc, int64_t N, int n, const hk_bu
     HK_CHECK_LAUNCH();
 
     std::vector<HostNode> nodes;
+    std::vector<TreeRec> tree;
     {
         HostNode root;
         root.off = 0;
         root.cnt = N;
         for (int i = 0; i < kRootSegments; ++i) root.seg_end.push_back(n / kRootSegments * (i + 1));
+        root.tid = 0;
         nodes.push_back(root);
+        TreeRec r;
+        r.off = 0;
+        r.cnt = N;
+        r.seg_end = root.seg_end;
+        tree.push_back(r);
     }
 
     DevBuf<EvalNode> d_enodes;
@@ -571,6 +624,19 @@ void build_index(hk_index *idx, const float *Xsrc, int64_t N, int n, const hk_bu
             R.off = nodes[p].off + nl[p];
             R.cnt = nodes[p].cnt - nl[p];
             R.seg_end = cs;
+            const int32_t pt = nodes[p].tid;
+            for (HostNode *c : {&L, &R}) {
+                c->tid = (int32_t)tree.size();
+                TreeRec r;
+                r.off = c->off;
+                r.cnt = c->cnt;
+                r.seg_end = cs;
+                r.parent = pt;
+                r.level = tree[pt].level + 1;
+                tree.push_back(r);
+            }
+            tree[pt].left = L.tid;
+            tree[pt].right = R.tid;
             next.push_back(L);
             next.push_back(R);
         }
@@ -615,6 +681,55 @@ void build_index(hk_index *idx, const float *Xsrc, int64_t N, int n, const hk_bu
     }
     idx->h_leaf_off[L] = N;
     idx->max_m = max_m;
+    // internal nodes: unified node ids are leaves 0..L-1 (position order),
+    // then internal nodes L..T-1 in creation order (parents before children)
+    std::vector<int32_t> uid(tree.size(), -1);
+    for (int64_t p = 0; p < L; ++p) uid[nodes[p].tid] = (int32_t)p;
+    int32_t next_id = (int32_t)L;
+    for (size_t t = 0; t < tree.size(); ++t)
+        if (tree[t].left >= 0) uid[t] = next_id++;
+    const int64_t T = next_id, I = T - L;
+    idx->T = T;
+    idx->h_tree_parent.assign(T, -1);
+    idx->h_tree_left.assign(T, -1);
+    idx->h_tree_right.assign(T, -1);
+    idx->h_tree_level.assign(T, 0);
+    idx->h_tree_beg.assign(T, 0);
+    idx->h_tree_end.assign(T, 0);
+    idx->h_inode_nseg.assign(I, 0);
+    idx->h_inode_seg_end.assign(I * kMaxSeg, 0);
+    idx->h_inode_seg.assign(I * kMaxSeg, 0);
+    std::vector<int32_t> &inode_seg = idx->h_inode_seg;
+    for (size_t t = 0; t < tree.size(); ++t) {
+        const TreeRec &r = tree[t];
+        const int32_t u = uid[t];
+        idx->h_tree_parent[u] = r.parent >= 0 ? uid[r.parent] : -1;
+        idx->h_tree_left[u] = r.left >= 0 ? uid[r.left] : -1;
+        idx->h_tree_right[u] = r.right >= 0 ? uid[r.right] : -1;
+        idx->h_tree_level[u] = r.level;
+        idx->h_tree_beg[u] = r.off;
+        idx->h_tree_end[u] = r.off + r.cnt;
+        if (u < L) continue;
+        const int64_t j0 = u - L;
+        const int m = (int)r.seg_end.size();
+        idx->h_inode_nseg[j0] = m;
+        int a = 0;
+        for (int j = 0; j < m; ++j) {
+            const int b = r.seg_end[j];
+            idx->h_inode_seg_end[j0 * kMaxSeg + j] = b;
+            auto key = std::make_pair(a, b);
+            auto it = segid.find(key);
+            int id;
+            if (it == segid.end()) {
+                id = (int)segid.size();
+                segid.emplace(key, id);
+            } else {
+                id = it->second;
+            }
+            inode_seg[j0 * kMaxSeg + j] = id;
+            a = b;
+        }
+    }
     idx->S = (int64_t)segid.size();
     std::vector<int32_t> seg_ab(2 * segid.size());
     for (auto &kv : segid) {
@@ -649,9 +764,20 @@ void build_index(hk_index *idx, const float *Xsrc, int64_t N, int n, const hk_bu
     ids.release();
 
     // ---- synopses and iSAX words (LSDFile)
-    k_envelope<<<(unsigned)L, 256, 0, s>>>(idx->X.p, n, idx->leaf_off.p, idx->leaf_nseg.p,
-                                           d_seg_end.p, idx->env.p);
+    k_envelope<<<(unsigned)L, 256, 0, s>>>(idx->X.p, n, idx->leaf_off.p, idx->leaf_off.p + 1,
+                                           idx->leaf_nseg.p, d_seg_end.p, idx->env.p);
     HK_CHECK_LAUNCH();
+    upload_tree(idx, s);
+    if (I > 0) {
+        DevBuf<int32_t> d_iseg_end;
+        d_iseg_end.alloc(I * kMaxSeg, s);
+        HK_CHECK_CUDA(cudaMemcpyAsync(d_iseg_end.p, idx->h_inode_seg_end.data(), I * kMaxSeg * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, s));
+        k_envelope<<<(unsigned)I, 256, 0, s>>>(idx->X.p, n, idx->tree_beg.p + L, idx->tree_end.p + L,
+                                               idx->inode_nseg.p, d_iseg_end.p, idx->ienv.p);
+        HK_CHECK_LAUNCH();
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
     float hbp[255];
     isax_breakpoints(hbp);
     idx->bp.alloc(255, s);

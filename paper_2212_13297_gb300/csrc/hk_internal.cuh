@@ -140,6 +140,7 @@ struct Workspace {
     DevBuf<float> cand_lb;      // nq * cand_C  lower bound D~ - E
     DevBuf<uint32_t> Uinit;     // retry pass: starting bounds
     DevBuf<int32_t> sel;        // retry pass: rows of the batch it answers
+    DevBuf<uint8_t> tree_alive; // HK_Q_TREE: T * nq, node-major: node stays for the query
     // graph mode: the captured pass (reading Q, writing out_*) and its key
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[4] = {0, 0, 0, 0};
@@ -159,6 +160,18 @@ struct Workspace {
         if (gexec) cudaGraphExecDestroy(gexec);
         gexec = nullptr;
     }
+};
+
+// Work space of DTW queries (hk_dtw.cu).
+constexpr int kDtwMaxBand = 16;      // largest Sakoe-Chiba half-width
+struct DtwWork {
+    DevBuf<float> envL, envU, paa, pool_d, out_dist;
+    DevBuf<double> qseg, lb, rs;
+    DevBuf<uint8_t> mask, sel;
+    DevBuf<int64_t> list, out_ids;
+    DevBuf<uint32_t> U;
+    DevBuf<int32_t> pool_p, pool_cnt, qflag, ctr;
+    DevBuf<long long> stats;
 };
 
 // Device view of a collection laid out by leaves (an index, or a plain
@@ -229,6 +242,7 @@ struct hk_index {
     hk::Workspace ws;
     hk::Workspace ws_retry;
     hk::Workspace ws_graph;    // HK_Q_GRAPH calls only: its buffers stay where the graph points
+    hk::DtwWork dtw;           // hk_query_dtw
 };
 
 namespace hk {
@@ -248,6 +262,9 @@ void run_query_ws(hk_index *idx, Workspace &ws, Workspace &ws_retry, const float
                   hk_query_stats *stats);
 void run_scan(const float *Xdev, int64_t N, int n, const float *Qdev, int nq, int k,
               cudaStream_t s, int64_t *out_ids, float *out_dist);
+// DTW (hk_dtw.cu)
+void run_query_dtw(hk_index *idx, const float *Qd, int nq, int k, int band, const hk_query_opts &o,
+                   cudaStream_t s, int64_t *out_ids, float *out_dist, hk_query_stats *stats);
 void debug_lb_eapca(hk_index *idx, const float *Qdev, int nq, double *out_host);
 void debug_lb_sax(hk_index *idx, const float *Qdev, int nq, float *out_host);
 void debug_tc_dist(hk_index *idx, const float *Qdev, int nq, float *lo_host, float *up_host);

@@ -9,12 +9,13 @@
 
 namespace {
 
-constexpr char kTag[8] = {'H', 'K', 'I', 'D', 'X', '0', '0', '1'};
+constexpr char kTag[8] = {'H', 'K', 'I', 'D', 'X', '0', '0', '2'};
 constexpr size_t kStage = (size_t)64 << 20;   // bytes per host staging copy
 
 struct Header {
     int64_t N, n, tau, eval_cap, L, max_m, depth, S, Npad, has_bf16, fmt16;
     double xn_max;
+    int64_t T;   // tree nodes (leaves and internal)
 };
 
 struct Fnv {
@@ -94,6 +95,7 @@ struct Part {
 
 std::vector<Part> parts(hk_index *x) {
     const size_t N = (size_t)x->N, n = (size_t)x->n, L = (size_t)x->L, S = (size_t)x->S;
+    const size_t T = (size_t)x->T, I = T - L;
     std::vector<Part> v = {
         {x->X.p, N * n * sizeof(float), true},
         {x->perm.p, N * sizeof(int64_t), true},
@@ -107,6 +109,17 @@ std::vector<Part> parts(hk_index *x) {
         {x->h_leaf_off.data(), (L + 1) * sizeof(int64_t), false},
         {x->h_leaf_nseg.data(), L * sizeof(int32_t), false},
         {x->h_seg_end.data(), L * hk::kMaxSeg * sizeof(int32_t), false},
+        // the tree (HTree): links, levels, position ranges, internal segmentations and synopses
+        {x->h_tree_parent.data(), T * sizeof(int32_t), false},
+        {x->h_tree_left.data(), T * sizeof(int32_t), false},
+        {x->h_tree_right.data(), T * sizeof(int32_t), false},
+        {x->h_tree_level.data(), T * sizeof(int32_t), false},
+        {x->h_tree_beg.data(), T * sizeof(int64_t), false},
+        {x->h_tree_end.data(), T * sizeof(int64_t), false},
+        {x->h_inode_nseg.data(), I * sizeof(int32_t), false},
+        {x->h_inode_seg_end.data(), I * hk::kMaxSeg * sizeof(int32_t), false},
+        {x->h_inode_seg.data(), I * hk::kMaxSeg * sizeof(int32_t), false},
+        {x->ienv.p, I * hk::kMaxSeg * 4 * sizeof(double), true},
     };
     if (x->has_bf16) {
         v.push_back({x->Xb.p, (size_t)x->Npad * n * sizeof(uint16_t), true});
@@ -127,7 +140,7 @@ int hk_save(const hk_index *idx, const char *path) {
         F.f = std::fopen(path, "wb");
         if (!F.f) hk::fail(HK_EIO, "cannot open %s for writing", path);
         Header h{idx->N, idx->n, idx->tau, idx->eval_cap, idx->L, idx->max_m, idx->depth, idx->S,
-                 idx->Npad, idx->has_bf16 ? 1 : 0, idx->fmt16, idx->xn_max};
+                 idx->Npad, idx->has_bf16 ? 1 : 0, idx->fmt16, idx->xn_max, idx->T};
         put(F, kTag, sizeof(kTag));
         put(F, &h, sizeof(h));
         HK_CHECK_CUDA(cudaDeviceSynchronize());
@@ -163,9 +176,10 @@ int hk_load(const char *path, void *stream, hk_index **out) {
         get(F, &h, sizeof(h));
         const bool ok = h.N >= 1 && h.N <= 0x7fffffffLL && h.n >= HK_MIN_LEN && h.n <= HK_MAX_LEN &&
                         h.n % HK_ISAX_SEGMENTS == 0 && h.L >= 1 && h.L <= h.N && h.S >= 1 &&
-                        h.S <= h.L * hk::kMaxSeg && h.max_m >= 1 && h.max_m <= hk::kMaxSeg && h.tau >= 1 &&
+                        h.S <= (2 * h.L - 1) * hk::kMaxSeg && h.max_m >= 1 && h.max_m <= hk::kMaxSeg && h.tau >= 1 &&
                         (h.has_bf16 == 0 || h.has_bf16 == 1) && (h.fmt16 == hk::kFmtF16 || h.fmt16 == hk::kFmtBF16) &&
-                        (h.has_bf16 == 0 || h.Npad >= h.N);
+                        (h.has_bf16 == 0 || h.Npad >= h.N) && h.T == 2 * h.L - 1 && h.depth >= 0 &&
+                        h.depth < h.T;
         if (!ok) hk::fail(HK_EINVAL, "%s: inconsistent header", path);
         cudaStream_t s = (cudaStream_t)stream;
         std::unique_ptr<hk_index> idx(new hk_index());
@@ -195,6 +209,18 @@ int hk_load(const char *path, void *stream, hk_index **out) {
         idx->h_leaf_off.resize(L + 1);
         idx->h_leaf_nseg.resize(L);
         idx->h_seg_end.resize(L * hk::kMaxSeg);
+        const size_t T = (size_t)h.T, I = T - L;
+        idx->T = h.T;
+        idx->h_tree_parent.resize(T);
+        idx->h_tree_left.resize(T);
+        idx->h_tree_right.resize(T);
+        idx->h_tree_level.resize(T);
+        idx->h_tree_beg.resize(T);
+        idx->h_tree_end.resize(T);
+        idx->h_inode_nseg.resize(I);
+        idx->h_inode_seg_end.resize(I * hk::kMaxSeg);
+        idx->h_inode_seg.resize(I * hk::kMaxSeg);
+        idx->ienv.alloc(I * hk::kMaxSeg * 4, s);
         if (idx->has_bf16) {
             idx->Xb.alloc((size_t)h.Npad * n, s);
             idx->xq.alloc((size_t)h.Npad, s);
@@ -213,6 +239,25 @@ int hk_load(const char *path, void *stream, hk_index **out) {
             if (idx->h_leaf_off[i + 1] < idx->h_leaf_off[i] || idx->h_leaf_nseg[i] < 1 ||
                 idx->h_leaf_nseg[i] > hk::kMaxSeg)
                 hk::fail(HK_EINVAL, "%s: inconsistent leaf table", path);
+        // the tree: children of internal nodes are valid later ids, leaves
+        // have none, ranges lie inside [0, N), levels fit the depth
+        for (size_t u = 0; u < T; ++u) {
+            const int32_t lf = idx->h_tree_left[u], rt = idx->h_tree_right[u];
+            const bool internal = u >= L;
+            const bool links = internal ? (lf >= 0 && rt >= 0 && (size_t)lf < T && (size_t)rt < T &&
+                                           idx->h_tree_parent[lf] == (int32_t)u &&
+                                           idx->h_tree_parent[rt] == (int32_t)u)
+                                        : (lf == -1 && rt == -1);
+            const bool range = idx->h_tree_beg[u] >= 0 && idx->h_tree_beg[u] < idx->h_tree_end[u] &&
+                               idx->h_tree_end[u] <= h.N;
+            const bool level = idx->h_tree_level[u] >= 0 && idx->h_tree_level[u] <= h.depth;
+            const bool segs = !internal || (idx->h_inode_nseg[u - L] >= 1 && idx->h_inode_nseg[u - L] <= hk::kMaxSeg);
+            if (!links || !range || !level || !segs) hk::fail(HK_EINVAL, "%s: inconsistent tree table", path);
+        }
+        for (size_t j = 0; j < I * hk::kMaxSeg; ++j)
+            if (idx->h_inode_seg[j] < 0 || idx->h_inode_seg[j] >= h.S)
+                hk::fail(HK_EINVAL, "%s: inconsistent tree table", path);
+        hk::upload_tree(idx.get(), s);
         *out = idx.release();
         return HK_OK;
     } catch (const hk::Error &e) {

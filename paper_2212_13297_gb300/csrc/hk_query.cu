@@ -52,14 +52,15 @@ constexpr int kSlack = 32;     // room for near-ties beyond k in an item list
 constexpr int kRing = 2;       // scan: chunks (2 KB per warp) in flight per warp
 constexpr int kRound1Leaves = 8;   // precision form, k > 16: leaves per query in the first round
 constexpr int kMaxG = 8;
-constexpr int kStatSlots = 24;
+constexpr int kStatSlots = 32;
 constexpr int kAmax = 256;     // most leaves the approximate step visits
 
 enum StatIdx {
     ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_APPROX, ST_LEAVES_CAND, ST_SERIES_CAND,
     ST_SAX_PRUNED, ST_ABANDONED, ST_FULL, ST_POINTS, ST_RESCORED, ST_FALLBACK,
     ST_ITEMS, ST_SKIPSEQ, ST_SCAN_NS, ST_LAUNCHES, ST_SCAN_BYTES, ST_RETRIED, ST_TC_PAIRS,
-    ST_TC_CANDS, ST_TC_BYTES, ST_TCA_PAIRS, ST_TCA_CANDS, ST_TCA_BYTES, ST_TC_LEAF_BYTES, ST_COUNT
+    ST_TC_CANDS, ST_TC_BYTES, ST_TCA_PAIRS, ST_TCA_CANDS, ST_TCA_BYTES, ST_TC_LEAF_BYTES, ST_LB_EVALS,
+    ST_COUNT
 };
 static_assert(ST_COUNT <= kStatSlots, "stat slots");
 
@@ -148,34 +149,186 @@ __device__ __forceinline__ void sax_cells(uint4 w4, const float *B, float (&lo)[
     }
 }
 
-// a2: LB_EAPCA of every query to every leaf synopsis (binary64, the segment
-// sum in segment order, exactly the definition).
-__global__ void k_lb_eapca(const double *__restrict__ qseg, int64_t S,
-                           const int32_t *__restrict__ leaf_nseg, const int32_t *__restrict__ leaf_seg,
-                           const int32_t *__restrict__ seg_ab, const double *__restrict__ env,
-                           int64_t L, int nq, double *__restrict__ lb) {
-    const int64_t leaf = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (leaf >= L) return;
-    const int m = leaf_nseg[leaf];
-    for (int q = blockIdx.y; q < nq; q += gridDim.y) {
+// The synopses of every node of the tree: leaves 0..L-1 (leaf tables),
+// internal nodes L..T-1 (internal tables), links and levels.
+struct TreeView {
+    int64_t L, T;
+    const int32_t *leaf_nseg, *leaf_seg;    // L, L * kMaxSeg distinct-segment ids
+    const double *env;                      // L * kMaxSeg * 4
+    const int32_t *inode_nseg, *inode_seg;  // T - L, (T - L) * kMaxSeg
+    const double *ienv;                     // (T - L) * kMaxSeg * 4
+    const int32_t *seg_ab;                  // S * 2
+    const int32_t *parent, *left, *right;   // T
+    const int64_t *beg, *end;               // T: leaf-order position ranges
+};
+
+// LB_EAPCA (squared, binary64) of query q to node u's synopsis: the segment
+// sum in segment order, exactly the definition (Sec. 2, Sec. 3.4).
+__device__ __forceinline__ double node_lb(const TreeView &t, const double *__restrict__ qseg, int64_t S,
+                                          int q, int64_t u) {
+    const bool leaf = u < t.L;
+    const int64_t j0 = leaf ? u : u - t.L;
+    const int m = leaf ? t.leaf_nseg[j0] : t.inode_nseg[j0];
+    const int32_t *segs = (leaf ? t.leaf_seg : t.inode_seg) + j0 * kMaxSeg;
+    const double *env = (leaf ? t.env : t.ienv) + j0 * kMaxSeg * 4;
     double acc = 0.0;
     for (int j = 0; j < m; ++j) {
-        const int sid = leaf_seg[leaf * kMaxSeg + j];
-        const double l = (double)(seg_ab[2 * sid + 1] - seg_ab[2 * sid]);
+        const int sid = segs[j];
+        const double l = (double)(t.seg_ab[2 * sid + 1] - t.seg_ab[2 * sid]);
         const double mu = qseg[((int64_t)q * S + sid) * 2];
         const double sd = qseg[((int64_t)q * S + sid) * 2 + 1];
-        const double *z = env + (leaf * kMaxSeg + j) * 4;
+        const double *z = env + j * 4;
         const double dm = dist_to_range64(mu, z[0], z[1]);
         const double ds = dist_to_range64(sd, z[2], z[3]);
-        const double t = __dadd_rn(__dmul_rn(dm, dm), __dmul_rn(ds, ds));
-        acc = __dadd_rn(acc, __dmul_rn(l, t));
+        const double tt = __dadd_rn(__dmul_rn(dm, dm), __dmul_rn(ds, ds));
+        acc = __dadd_rn(acc, __dmul_rn(l, tt));
     }
-    lb[(int64_t)q * L + leaf] = acc;
-    }
+    return acc;
+}
+
+// a2: LB_EAPCA of every query to every leaf synopsis.
+__global__ void k_lb_eapca(const double *__restrict__ qseg, int64_t S, TreeView tv, int nq,
+                           double *__restrict__ lb) {
+    const int64_t leaf = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (leaf >= tv.L) return;
+    for (int q = blockIdx.y; q < nq; q += gridDim.y) lb[(int64_t)q * tv.L + leaf] = node_lb(tv, qseg, S, q, leaf);
 }
 
 // Certified lower value of a binary64 LB (absorbs its rounding).
 __device__ __forceinline__ double lb_lower(double lb) { return __dmul_rd(lb, 1.0 - 0x1p-40); }
+
+constexpr int kHeapCap = 512;   // tree mode: queue entries per query
+
+// a3 with HK_Q_TREE: the approximate search as the paper's best-first
+// traversal (Approx-kNN, Sec. 3.4): a priority queue of nodes keyed by
+// LB_EAPCA, starting at the root; an internal node taken from it puts its two
+// children in, a leaf taken from it is visited, until at least l_max leaves
+// and k series.  One thread per query walks its queue in shared memory (four
+// queries per block).  A full queue drops the node being added; if the queue
+// then runs dry before k series, the remaining leaves are taken in ascending
+// leaf-LB order.  Any visited leaves give a valid bound U.
+__global__ void __launch_bounds__(128) k_tree_approx(const double *__restrict__ qseg, int64_t S, TreeView tv,
+                                                     int root, int l_max, int k, int nq, int amax,
+                                                     int32_t *__restrict__ approx, int32_t *__restrict__ napprox,
+                                                     uint8_t *__restrict__ mask, double *__restrict__ lb,
+                                                     long long *__restrict__ stats) {
+    __shared__ double keys_s[4][kHeapCap];
+    __shared__ int32_t node_s[4][kHeapCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 4 + warp;
+    if (q >= nq || lane != 0) return;
+    double *hk = keys_s[warp];
+    int32_t *hn = node_s[warp];
+    int hs = 0;
+    auto less = [&](int i, int j) { return hk[i] < hk[j] || (hk[i] == hk[j] && hn[i] < hn[j]); };
+    auto swap = [&](int i, int j) {
+        const double a = hk[i]; hk[i] = hk[j]; hk[j] = a;
+        const int32_t b = hn[i]; hn[i] = hn[j]; hn[j] = b;
+    };
+    auto push = [&](double key, int32_t node) {
+        int i = hs++;
+        hk[i] = key;
+        hn[i] = node;
+        while (i > 0 && less(i, (i - 1) / 2)) {
+            swap(i, (i - 1) / 2);
+            i = (i - 1) / 2;
+        }
+    };
+    auto pop = [&](double &key, int32_t &node) {
+        key = hk[0];
+        node = hn[0];
+        --hs;
+        hk[0] = hk[hs];
+        hn[0] = hn[hs];
+        int i = 0;
+        for (;;) {
+            const int l = 2 * i + 1, r = l + 1;
+            int m = i;
+            if (l < hs && less(l, m)) m = l;
+            if (r < hs && less(r, m)) m = r;
+            if (m == i) break;
+            swap(i, m);
+            i = m;
+        }
+    };
+    long long evals = 1;
+    push(node_lb(tv, qseg, S, q, root), root);
+    int nch = 0;
+    long long covered = 0;
+    while (hs > 0 && nch < amax && (nch < l_max || covered < k)) {
+        double key;
+        int32_t u;
+        pop(key, u);
+        if (u < tv.L) {
+            approx[(int64_t)q * amax + nch++] = u;
+            mask[(int64_t)u * nq + q] = 1;
+            covered += tv.end[u] - tv.beg[u];
+            lb[(int64_t)q * tv.L + u] = key;
+        } else {
+            for (int c = 0; c < 2; ++c) {
+                const int32_t v = c ? tv.right[u] : tv.left[u];
+                const double key_v = node_lb(tv, qseg, S, q, v);
+                ++evals;
+                if (hs < kHeapCap) push(key_v, v);
+            }
+        }
+    }
+    while (nch < amax && covered < k) {
+        // the queue ran dry after dropping nodes: ascending (leaf LB, leaf)
+        double best = INFINITY;
+        int64_t bl = -1;
+        for (int64_t f = 0; f < tv.L; ++f) {
+            if (mask[f * nq + q] != 0) continue;
+            const double v = node_lb(tv, qseg, S, q, f);
+            ++evals;
+            if (bl < 0 || v < best) { best = v; bl = f; }
+        }
+        if (bl < 0) break;
+        approx[(int64_t)q * amax + nch++] = (int32_t)bl;
+        mask[bl * nq + q] = 1;
+        covered += tv.end[bl] - tv.beg[bl];
+        lb[(int64_t)q * tv.L + bl] = best;
+    }
+    napprox[q] = nch;
+    stat_add(&stats[ST_LB_EVALS], evals);
+}
+
+// a4 with HK_Q_TREE: candidate leaves by a top-down pass over the tree
+// (FindCandidateLeaves over the hierarchy of node synopses, Sec. 3.3-3.4).
+// At one level, a node's LB_EAPCA is evaluated for a query only if the
+// node's parent stayed for it (the root always), and the node stays unless
+// its certified LB exceeds U: every series below a node is at least its LB
+// away, so a pruned node prunes its whole subtree.  A leaf that stays
+// becomes a candidate unless the approximate search visited it.
+// alive[node * nq + q], node-major.
+__global__ void k_tree_level(const double *__restrict__ qseg, int64_t S, TreeView tv,
+                             const int32_t *__restrict__ nodes, int cnt, int nq, const uint32_t *__restrict__ U,
+                             uint8_t *__restrict__ alive, uint8_t *__restrict__ mask, int32_t *__restrict__ qcand,
+                             double *__restrict__ lb, long long *__restrict__ stats) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    long long ev = 0;
+    if (t < (int64_t)cnt * nq) {
+        const int64_t u = nodes[t / nq];
+        const int q = (int)(t % nq);
+        const int32_t p = tv.parent[u];
+        uint8_t a = 0;
+        if (p < 0 || alive[(int64_t)p * nq + q]) {
+            const double v = node_lb(tv, qseg, S, q, u);
+            ev = 1;
+            a = !(lb_lower(v) > (double)__uint_as_float(U[q]));
+            if (u < tv.L) {
+                lb[(int64_t)q * tv.L + u] = v;
+                if (a && mask[u * nq + q] == 0) {
+                    mask[u * nq + q] = 2;
+                    atomicAdd(&qcand[q], 1);
+                }
+            }
+        }
+        alive[u * nq + q] = a;
+    }
+    ev = warp_sum_ll(ev);
+    if ((threadIdx.x & 31) == 0 && ev) stat_add(&stats[ST_LB_EVALS], ev);
+}
 
 // a3 (selection): the leaves the approximate search visits: ascending
 // (LB_EAPCA, leaf) until at least l_max leaves and at least k series.
@@ -386,6 +539,13 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// max(a, b, c) in one instruction (three-input max.f32, sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Packed float32 pairs (the f32x2 pipes): a += (q - x)^2 lane-wise.
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
     uint64_t r;
@@ -551,7 +711,7 @@ __global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
                             float a0, a1, b0, b1;
                             unpack2(a2, a0, a1);
                             unpack2(b2, b0, b1);
-                            acc2 = sqacc_rd2(pack2(fmaxf(fmaxf(a0, b0), 0.0f), fmaxf(fmaxf(a1, b1), 0.0f)), acc2);
+                            acc2 = sqacc_rd2(pack2(max3f(a0, b0, 0.0f), max3f(a1, b1, 0.0f)), acc2);
                         }
                         float l0, l1;
                         unpack2(acc2, l0, l1);
@@ -631,10 +791,10 @@ __global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
                         unpack2(a, a0, a1);
                         unpack2(b, b0, b1);
                         acc[g] = (a0 + a1) + (b0 + b1);
-                        my_pts += 16;
                         if (acc[g] > T[g]) {
                             act &= ~(1u << g);
                             ++my_ab;
+                            my_pts += 16 * (c + 1);
                         }
                     }
                 }
@@ -648,6 +808,7 @@ __global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
                 for (int g = 0; g < G; ++g) {
                     if (!(act >> g & 1)) continue;
                     ++my_full;
+                    my_pts += n;
                     const int slot = atomicAdd(&s_stage[g], 1);
                     stage_d[g * kBT + slot] = acc[g];
                     stage_p[g * kBT + slot] = (int32_t)s;
@@ -759,10 +920,11 @@ __global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {
 }
 
 // U = min(U, (1+rho) x k-th smallest pooled float32 distance).
-__global__ void k_stats_init(long long *__restrict__ stats, int nq, long long L) {
+__global__ void k_stats_init(long long *__restrict__ stats, int nq, long long L, long long lb_evals) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         stats[ST_QUERIES] = nq;
         stats[ST_LEAVES_TOTAL] = (long long)nq * L;
+        stats[ST_LB_EVALS] = lb_evals;
     }
 }
 
@@ -1067,6 +1229,25 @@ int sm_count() {
     return sms;
 }
 
+TreeView tree_view(const hk_index *idx) {
+    TreeView t{};
+    t.L = idx->L;
+    t.T = idx->T;
+    t.leaf_nseg = idx->leaf_nseg.p;
+    t.leaf_seg = idx->leaf_seg.p;
+    t.env = idx->env.p;
+    t.inode_nseg = idx->inode_nseg.p;
+    t.inode_seg = idx->inode_seg.p;
+    t.ienv = idx->ienv.p;
+    t.seg_ab = idx->seg_ab.p;
+    t.parent = idx->tree_parent.p;
+    t.left = idx->tree_left.p;
+    t.right = idx->tree_right.p;
+    t.beg = idx->tree_beg.p;
+    t.end = idx->tree_end.p;
+    return t;
+}
+
 struct ScanConfig {
     int G;
     int p2;
@@ -1358,6 +1539,7 @@ void copy_stats(const Workspace &ws, hk_query_stats *stats, cudaStream_t s, Scan
     stats->tc_approx_pairs = st[ST_TCA_PAIRS];
     stats->tc_approx_bytes = st[ST_TCA_BYTES];
     stats->tc_leaf_bytes = st[ST_TC_LEAF_BYTES];
+    stats->lb_evaluations = st[ST_LB_EVALS];
     stats->scan_ns = timer ? timer->total_ns() : 0;
     stats->kernel_launches = launches;
 }
@@ -1414,6 +1596,8 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     const float rho = rho_for(n);
     const bool noprune = (o.flags & HK_Q_NOPRUNE) != 0;
     const bool tc = (o.flags & HK_Q_BF16) != 0;
+    const bool tree = (o.flags & HK_Q_TREE) != 0;
+    const TreeView tv = tree_view(idx);
     const bool nosax = noprune || tc || (o.flags & HK_Q_NOSAX) != 0;
     const int l_max = o.l_max > 0 ? o.l_max : kDefaultLMax;
     const float eapca_th = o.eapca_th >= 0 ? o.eapca_th : kDefaultEapcaTh;
@@ -1440,7 +1624,7 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
         k_fill_u32<<<64, 256, 0, s>>>(ws.U.p, nq, 0x7f800000u);
         HK_CHECK_LAUNCH();
     }
-    k_stats_init<<<1, 32, 0, s>>>((long long *)ws.stats.p, nq, L);
+    k_stats_init<<<1, 32, 0, s>>>((long long *)ws.stats.p, nq, L, tree ? 0 : (long long)nq * L);
     HK_CHECK_LAUNCH();
     HK_CHECK_CUDA(cudaMemsetAsync(ws.counters.p, 0, 4 * sizeof(int32_t), s));
 
@@ -1465,10 +1649,11 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     k_qprep<<<nq, 256, n * sizeof(float), s>>>(Qd, n, idx->seg_ab.p, idx->S, ws.qseg.p,
                                                nosax ? nullptr : ws.sax_paa.p);
     HK_CHECK_LAUNCH();
-    k_lb_eapca<<<dim3((unsigned)((L + 127) / 128), std::min(nq, 65535)), 128, 0, s>>>(
-        ws.qseg.p, idx->S, idx->leaf_nseg.p, idx->leaf_seg.p, idx->seg_ab.p, idx->env.p, L, nq,
-        ws.lb.p);
-    HK_CHECK_LAUNCH();
+    if (!tree) {
+        k_lb_eapca<<<dim3((unsigned)((L + 127) / 128), std::min(nq, 65535)), 128, 0, s>>>(
+            ws.qseg.p, idx->S, tv, nq, ws.lb.p);
+        HK_CHECK_LAUNCH();
+    }
 
     LeafView v;
     v.X = idx->X.p;
@@ -1503,8 +1688,15 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
 
     // a3: approximate search (no LB_SAX: these leaves are scanned whole)
     if (!noprune && !U_init) {
-        k_approx_select<<<nq, 256, 0, s>>>(ws.lb.p, L, idx->leaf_off.p, l_max, k, nq, kAmax, ws.approx.p,
-                                           ws.qcand.p, ws.mask.p);
+        if (tree) {
+            const int root = L > 1 ? (int)L : 0;   // the first internal node, or the only leaf
+            k_tree_approx<<<(nq + 3) / 4, 128, 0, s>>>(ws.qseg.p, idx->S, tv, root, l_max, k, nq, kAmax,
+                                                      ws.approx.p, ws.qcand.p, ws.mask.p, ws.lb.p,
+                                                      (long long *)ws.stats.p);
+        } else {
+            k_approx_select<<<nq, 256, 0, s>>>(ws.lb.p, L, idx->leaf_off.p, l_max, k, nq, kAmax, ws.approx.p,
+                                               ws.qcand.p, ws.mask.p);
+        }
         HK_CHECK_LAUNCH();
         if (tc && k <= kTcLocalK) {
             // on the tensor cores from U = +inf: each thread's k best upper
@@ -1528,10 +1720,23 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     // a4: candidate leaves, per-query mode
     {
         const int64_t pairs = L * (int64_t)nq;
-        k_mask_candidates<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(ws.lb.p, L, nq, ws.U.p,
-                                                                        noprune ? 1 : 0, ws.mask.p,
-                                                                        ws.qcand.p);
-        HK_CHECK_LAUNCH();
+        if (tree) {
+            ws.tree_alive.reserve((size_t)idx->T * nq, s);
+            const int levels = (int)idx->h_level_off.size() - 1;
+            for (int d = 0; d < levels; ++d) {
+                const int cnt = idx->h_level_off[d + 1] - idx->h_level_off[d];
+                const int64_t work = (int64_t)cnt * nq;
+                k_tree_level<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(
+                    ws.qseg.p, idx->S, tv, idx->level_nodes.p + idx->h_level_off[d], cnt, nq, ws.U.p,
+                    ws.tree_alive.p, ws.mask.p, ws.qcand.p, ws.lb.p, (long long *)ws.stats.p);
+                HK_CHECK_LAUNCH();
+            }
+        } else {
+            k_mask_candidates<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(ws.lb.p, L, nq, ws.U.p,
+                                                                            noprune ? 1 : 0, ws.mask.p,
+                                                                            ws.qcand.p);
+            HK_CHECK_LAUNCH();
+        }
         k_qmode<<<(nq + 255) / 256, 256, 0, s>>>(ws.qcand.p, L, nq, eapca_th, nosax ? 1 : 0,
                                                  (o.flags & HK_Q_NOTHRESH) ? 1 : 0, ws.qmode.p,
                                                  (long long *)ws.stats.p);
@@ -2005,8 +2210,7 @@ void debug_lb_eapca(hk_index *idx, const float *Qd, int nq, double *out_host) {
     k_qprep<<<nq, 256, idx->n * sizeof(float), s>>>(Qd, idx->n, idx->seg_ab.p, idx->S, ws.qseg.p, nullptr);
     HK_CHECK_LAUNCH();
     k_lb_eapca<<<dim3((unsigned)((idx->L + 127) / 128), std::min(nq, 65535)), 128, 0, s>>>(
-        ws.qseg.p, idx->S, idx->leaf_nseg.p, idx->leaf_seg.p, idx->seg_ab.p, idx->env.p, idx->L, nq,
-        ws.lb.p);
+        ws.qseg.p, idx->S, tree_view(idx), nq, ws.lb.p);
     HK_CHECK_LAUNCH();
     HK_CHECK_CUDA(cudaMemcpyAsync(out_host, ws.lb.p, (size_t)nq * idx->L * sizeof(double),
                                   cudaMemcpyDeviceToHost, s));

@@ -315,6 +315,10 @@ __device__ void fetch_item(const TcArgs &A, int64_t total, TcItem &D, int lane) 
 }  // namespace
 
 // One CTA per SM; loops over (leaf, query block, series range) items.
+// kHooks: the test hooks of the bounded waits (a wait limit from the
+// arguments, an epilogue warp stalled on a barrier nothing arrives at); the
+// ordinary launch is compiled without them.
+template <bool kHooks>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     const int n = A.n;
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     // running counts of barrier completions (phases), kept per role
     uint32_t g_tile = 0;   // tiles processed by this CTA so far (all roles agree)
     uint32_t issued = 0;   // producer: tiles whose copies it issued; MMA warp: tiles it committed
-    const uint64_t wait_ns = A.wait_ns ? A.wait_ns : kWaitNs;
+    const uint64_t wait_ns = (kHooks && A.wait_ns) ? A.wait_ns : kWaitNs;
     long long my_cand = 0, my_pairs = 0, my_bytes = 0;
 
     // Items are claimed when a CTA is ready for one, so the query blocks of
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
             long long pairs = 0;
             // test hook: one epilogue warp waits for a barrier nothing
             // arrives at, so its bounded wait runs out and the CTA aborts
-            const bool stalled = A.dbg_stall && warp == 2 && g_tile == 0 &&
+            const bool stalled = kHooks && A.dbg_stall && warp == 2 && g_tile == 0 &&
                                  !mbar_wait_warp(&S.never, 0, &S.abort_flag, wait_ns);
             for (int t = 0; t < T && !stalled; ++t) {
                 const uint32_t gt = g_tile + t;
@@ -821,13 +825,18 @@ void launch_tc_scan(const TcArgs &a, cudaStream_t s) {
     const size_t smem = tc_smem_bytes(a.n);
     static std::once_flag once;
     std::call_once(once, [] {
-        HK_CHECK_CUDA(cudaFuncSetAttribute(k_tc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HK_CHECK_CUDA(cudaFuncSetAttribute(k_tc_scan<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)tc_smem_bytes(256)));
+        HK_CHECK_CUDA(cudaFuncSetAttribute(k_tc_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)tc_smem_bytes(256)));
     });
     int dev = 0, sms = 0;
     HK_CHECK_CUDA(cudaGetDevice(&dev));
     HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    k_tc_scan<<<sms, kTcThreads, smem, s>>>(a);
+    if (a.wait_ns || a.dbg_stall)
+        k_tc_scan<true><<<sms, kTcThreads, smem, s>>>(a);
+    else
+        k_tc_scan<false><<<sms, kTcThreads, smem, s>>>(a);
     HK_CHECK_LAUNCH();
 }
 

@@ -26,8 +26,8 @@ def test_load_rejects_missing_and_foreign_files(hb, tmp_path):
     assert e.value.code == hb.HK_EINVAL
     # the right tag but a header that describes no valid index
     hdr = tmp_path / "header.hkidx"
-    hdr.write_bytes(b"HKIDX001" + np.array([0, 7, 0, 0, 0, 0, 0, 0, 0, 0, 9], np.int64).tobytes()
-                    + np.float64(0).tobytes())
+    hdr.write_bytes(b"HKIDX002" + np.array([0, 7, 0, 0, 0, 0, 0, 0, 0, 0, 9], np.int64).tobytes()
+                    + np.float64(0).tobytes() + np.int64(1).tobytes())
     with pytest.raises(hb.HerculesError) as e:
         hb.Index.load(hdr)
     assert e.value.code == hb.HK_EINVAL
