@@ -40,6 +40,8 @@ WORKLOADS = {
                       desc="2M random walks x 256, leaf 20K, 1000 hard queries (sigma 0.5/1.0), k=10"),
     "tcleaf100k": dict(N=4_000_000, n=256, tau=100_000, nq=1000, sigmas=[0.5, 1.0], k=10, batch=1000,
                        desc="4M random walks x 256, leaf 100K, 1000 hard queries (sigma 0.5/1.0), k=10"),
+    "tcleaf100k2k": dict(N=4_000_000, n=256, tau=100_000, nq=2000, sigmas=[0.5, 1.0], k=10, batch=2000,
+                         desc="4M random walks x 256, leaf 100K, 2000 hard queries (sigma 0.5/1.0), k=10"),
     "precprofile": dict(N=2_000_000, n=256, tau=10_000, nq=1024, sigmas=("uniform", 0.01, 1.0), k=100,
                         batch=1024,
                         desc="2M random walks x 256, leaf 10K, 1024 queries (sigma uniform in [0.01, 1.0]), k=100"),
@@ -239,18 +241,20 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def serve(binding, idx, Q_all, k, max_batch, qflags, rate, seconds, form):
+def serve(binding, idx, Q_all, k, max_batch, qflags, rate, seconds, form, persistent=0):
     """Open-loop serving: requests arrive one query at a time (Poisson at
     `rate` requests/s for `seconds`) and are answered by the
-    continuous-batching server; reports arrival-to-answer latency and the
-    rate at which answers came back."""
+    continuous-batching server (batch-level, or with the tensor-core scans of
+    all batches in flight in one resident launch when `persistent`); reports
+    arrival-to-answer latency and the rate at which answers came back."""
     import threading
     import numpy as np
     Qh = Q_all.cpu().numpy()
     rng = np.random.default_rng(11)
     n_req = max(1, int(rate * seconds))
     gaps = rng.exponential(1.0 / rate, n_req)
-    sv = binding.Server(max_batch=max_batch, max_wait_us=0, query_flags=qflags, workers=2)
+    sv = binding.Server(max_batch=max_batch, max_wait_us=0, query_flags=qflags,
+                        workers=4 if persistent else 2, persistent=persistent)
     coll = sv.add(idx)
     # warm the workers' buffers
     for t in [sv.submit(coll, Qh[i], k) for i in range(min(64, len(Qh)))]:
@@ -290,7 +294,10 @@ def serve(binding, idx, Q_all, k, max_batch, qflags, rate, seconds, form):
     st = sv.stats()
     sv.close()
     ls = np.sort(lat)
-    return dict(kind="open loop, Poisson arrivals, one query per request, 2 workers", form=form,
+    return dict(kind="open loop, Poisson arrivals, one query per request, %s" % (
+                    "persistent scan, 4 workers" if persistent else "batch-level, 2 workers"), form=form,
+                scan_launches=st["scan_launches"], scan_jobs=st["scan_jobs"],
+                scan_jobs_inflight=st["scan_jobs_inflight"],
                 offered_rate=rate, requests=n_req, answered_per_s=n_req / wall,
                 latency_ms=dict(p50=float(ls[n_req // 2]) * 1e3,
                                 p99=float(ls[min(n_req - 1, int(0.99 * n_req))]) * 1e3,
@@ -328,7 +335,8 @@ def serve_mix(args):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         builds.append(time.perf_counter() - t0)
-    sv = binding.Server(max_batch=1024, max_wait_us=0, query_flags=sv_flags, workers=2)
+    sv = binding.Server(max_batch=1024, max_wait_us=0, query_flags=sv_flags,
+                        workers=4 if args.persistent else 2, persistent=1 if args.persistent else 0)
     colls = [sv.add(ix) for ix in idxs]
     for ci in range(len(MIX)):   # warm each collection's path
         for t in [sv.submit(colls[ci], pools[ci][i], kk) for i, kk in enumerate((1, 10, 100))]:
@@ -386,8 +394,11 @@ def serve_mix(args):
                 latency_ms=dict(p50=pct(lat, 0.5), p99=pct(lat, 0.99), max=float(lat.max()) * 1e3),
                 per_collection=per, batches=st["batches"], mean_batch=st["served"] / max(1, st["batches"]),
                 max_batch=st["max_batch"], errors=st["errors"], data="synthetic",
+                scan_launches=st["scan_launches"], scan_jobs=st["scan_jobs"],
+                scan_jobs_inflight=st["scan_jobs_inflight"], scan_max_collections=st["scan_max_collections"],
                 config=dict(workload="served mix: " + "; ".join(m[0] for m in MIX), k=[1, 10, 100],
-                            sigma="uniform [0.01, 1.0]", arrivals="Poisson, seed 2", workers=2))
+                            sigma="uniform [0.01, 1.0]", arrivals="Poisson, seed 2",
+                            server="persistent scan, 4 workers" if args.persistent else "batch-level, 2 workers"))
     print(json.dumps(line), flush=True)
 
 
@@ -623,6 +634,8 @@ def main():
     ap.add_argument("--tree-leaf", type=int, default=1000)
     ap.add_argument("--dtw", action="store_true",
                     help="instead of the step benchmark, exact k-NN under DTW through the index")
+    ap.add_argument("--persistent", action="store_true",
+                    help="--serve-mix: serve with the resident tensor-core scan")
     ap.add_argument("--serve-mix", type=float, default=0.0,
                     help="instead of the step benchmark, serve the four-collection mix at this "
                          "rate (requests/s) and print its latency line")
@@ -771,6 +784,9 @@ def main():
         if args.serve > 0:
             serving[args.form] = serve(binding, idx, Q_all, k, B, qflags, args.serve, args.serve_seconds,
                                        args.form)
+            if args.form != "plain":
+                serving[args.form + "_persistent"] = serve(binding, idx, Q_all, k, B, qflags, args.serve,
+                                                           args.serve_seconds, args.form, persistent=1)
         if args.serve_plain > 0 and args.form != "plain":
             serving["plain"] = serve(binding, idx, Q_all, k, B, 0, args.serve_plain,
                                      args.serve_plain_seconds, "plain")

@@ -292,7 +292,14 @@ typedef struct {
                               0 = no cap                                        */
     uint32_t query_flags;  /* HK_Q_* applied to every batch (HK_Q_BF16 uses the
                               tensor-core form where the index has a copy)     */
-    int32_t workers;       /* concurrent batches (threads, CUDA streams); 0 = 2 */
+    int32_t workers;       /* concurrent batches (threads, CUDA streams); 0 = 2,
+                              or 4 with persistent                            */
+    int32_t persistent;    /* 1: the tensor-core scans of all batches in flight
+                              run in one resident launch that takes each
+                              batch's scan from a device-resident ring while
+                              it runs (batches of different collections and
+                              series lengths interleave in it); 0: each batch
+                              launches its own kernels                        */
 } hk_server_opts;
 
 typedef struct {
@@ -302,6 +309,11 @@ typedef struct {
     int64_t errors;        /* batches that failed                               */
     int64_t pending;       /* requests waiting for a batch                      */
     int64_t busy_ns;       /* summed wall time of the batches                   */
+    int64_t budget_peak;   /* most device bytes the batches in flight held      */
+    int64_t scan_launches; /* persistent: resident scan launches started        */
+    int64_t scan_jobs;     /* persistent: batch scans published to the ring     */
+    int64_t scan_jobs_inflight;  /* of those, published while a launch ran      */
+    int64_t scan_max_collections; /* most collections one launch served          */
 } hk_server_stats;
 
 /*
@@ -309,10 +321,14 @@ typedef struct {
  * continuous batching (Sec. 4.1: queries arrive asynchronously): each worker
  * takes the pending requests of one collection and answers them as one batch
  * with k = the batch's largest k; each request receives the first k_i entries,
- * which equal what hk_query returns for it alone.  Requests arriving while
- * batches run join the next batch.  The server does not own the indexes;
- * they must outlive it.  hk_server_destroy must not race with other calls on
- * the same server.
+ * which equal what hk_query returns for it alone.  A batch holds device
+ * memory from hbm_budget until it completes; a worker admits as many pending
+ * requests as the budget has room for beside the batches in flight (at least
+ * one when none is), else waits for memory to free up.  With persistent = 1
+ * the batches' tensor-core scans run in one resident launch, each admitted
+ * batch's scan joining it while it runs.  The server does not own the
+ * indexes; they must outlive it.  hk_server_destroy must not race with other
+ * calls on the same server.
  */
 int hk_server_create(const hk_server_opts *opts, hk_server **out);
 int hk_server_add(hk_server *sv, hk_index *idx, int32_t *coll_id);

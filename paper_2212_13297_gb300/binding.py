@@ -75,12 +75,13 @@ class hk_tune_result(ctypes.Structure):
 class hk_server_opts(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64), ("query_flags", ctypes.c_uint32),
-                ("workers", ctypes.c_int32)]
+                ("workers", ctypes.c_int32), ("persistent", ctypes.c_int32)]
 
 
 class hk_server_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
-        "batches", "served", "max_batch", "errors", "pending", "busy_ns")]
+        "batches", "served", "max_batch", "errors", "pending", "busy_ns", "budget_peak",
+        "scan_launches", "scan_jobs", "scan_jobs_inflight", "scan_max_collections")]
 
 
 class HerculesError(RuntimeError):
@@ -366,9 +367,9 @@ def scan_knn(X, Q, k: int, stream=None):
 class Server:
     """Continuous-batching server over registered indexes (hk_server_*)."""
 
-    def __init__(self, max_batch=0, max_wait_us=0, hbm_budget=0, query_flags=0, workers=0):
+    def __init__(self, max_batch=0, max_wait_us=0, hbm_budget=0, query_flags=0, workers=0, persistent=0):
         o = hk_server_opts(int(max_batch), int(max_wait_us), int(hbm_budget), int(query_flags),
-                           int(workers))
+                           int(workers), int(persistent))
         h = ctypes.c_void_p()
         _check(lib().hk_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -141,6 +141,7 @@ struct Workspace {
     DevBuf<uint32_t> Uinit;     // retry pass: starting bounds
     DevBuf<int32_t> sel;        // retry pass: rows of the batch it answers
     DevBuf<uint8_t> tree_alive; // HK_Q_TREE: T * nq, node-major: node stays for the query
+    struct TcEngine *engine = nullptr;   // served: tensor-core scans go to this resident launch
     // graph mode: the captured pass (reading Q, writing out_*) and its key
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[4] = {0, 0, 0, 0};
@@ -329,6 +330,39 @@ struct TcArgs {
 };
 // Test hooks of the tensor-core scan's bounded waits (hk_debug_tc_wait).
 void tc_wait_hooks(uint64_t &wait_ns, int &stall);
+
+// Served form of the tensor-core scan: one resident launch takes the scans
+// of many batches (jobs) from a ring as they are published.
+constexpr int kTcRing = 64;          // jobs in flight at most
+struct TcJob {                       // device memory, written before publication
+    TcArgs args;
+    int64_t total;                   // work items of the job (> 0)
+    uint32_t seq;                    // publication number
+    uint32_t pad;
+};
+struct TcServe {                     // the served launch's view of the ring
+    TcJob *jobs;                     // kTcRing
+    unsigned long long *word;        // (sequence of the current job << 32) | its next item
+    int32_t *done;                   // kTcRing items finished per slot
+    const volatile uint32_t *published;   // host-mapped: jobs published so far
+    volatile uint32_t *done_seq;     // host-mapped, kTcRing: last completed sequence per slot
+    uint64_t idle_ns;                // a CTA leaves after this long without work
+};
+struct TcEngine;                     // host side (hk_tc.cu)
+TcEngine *tc_engine_create(int spare_sms);
+void tc_engine_destroy(TcEngine *e);
+// Publish one scan (arguments as for launch_tc_scan, `items` work items) to
+// the served launch (starting it if none runs) and wait, bounded by
+// timeout_ns, until its items are done.  The caller's stream must have
+// produced the scan's inputs already (synchronised).
+void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout_ns);
+struct TcEngineStats {
+    long long launches;              // served launches started
+    long long jobs;                  // jobs published
+    long long jobs_inflight;         // of those, published while a launch was running
+    long long max_colls_per_launch;  // most distinct collections one launch served
+};
+void tc_engine_stats(TcEngine *e, TcEngineStats *out);
 void launch_tc_scan(const TcArgs &a, cudaStream_t s);
 constexpr int kFmtF16 = 0;    // tcgen05 kind::f16 operand encodings
 constexpr int kFmtBF16 = 1;

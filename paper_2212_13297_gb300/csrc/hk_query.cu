@@ -1401,9 +1401,18 @@ void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, 
     t.dbg_up = nullptr;
     t.N = idx->N;
     tc_wait_hooks(t.wait_ns, t.dbg_stall);
-    if (tctimer) tctimer->mark(s);
-    launch_tc_scan(t, s);
-    if (tctimer) tctimer->mark(s);
+    if (ws.engine && !capture) {
+        // served: the scan is a job of the resident launch, which also runs
+        // other batches' scans (its inputs must be ready first)
+        int64_t items = 0;
+        HK_CHECK_CUDA(cudaMemcpyAsync(&items, ws.item_off.p + v.L, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HK_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (items > 0) tc_engine_run(ws.engine, t, items, 120ull * 1000000000ull);
+    } else {
+        if (tctimer) tctimer->mark(s);
+        launch_tc_scan(t, s);
+        if (tctimer) tctimer->mark(s);
+    }
     k_pool_kth<<<nq, 512, 0, s>>>(ws.pool_d.p, ws.pool_cnt.p, pool_C, k, rho, ws.U.p);
     HK_CHECK_LAUNCH();
     launch_tc_rescore(Qd, v.X, n, nq, ws.cand_cnt.p, ws.cand_p.p, ws.cand_lb.p, cand_C, ws.U.p,

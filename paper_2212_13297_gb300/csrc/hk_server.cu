@@ -4,16 +4,30 @@
 // Queries); on one GPU throughput comes from answering many at once.  The
 // server keeps a FIFO of pending requests per registered collection.  Worker
 // threads (each with its own CUDA stream and query work space) repeatedly
-// take the pending requests of one collection -- up to a batch size that fits
-// the device-memory budget -- and answer them together with the exact query
-// path, using k = the largest k of the batch: answers are totally ordered by
-// (binary64 squared distance, id), so each request's answer is the prefix of
-// length k_i, exactly what a call for that request alone returns.  Requests
-// that arrive while batches are on the GPU wait for the next batch; with two
-// workers, one batch's copies and host work overlap another's kernels.
+// take the pending requests of one collection and answer them together with
+// the exact query path, using k = the largest k of the batch: answers are
+// totally ordered by (binary64 squared distance, id), so each request's
+// answer is the prefix of length k_i, exactly what a call for that request
+// alone returns.
 //
-// Every wait is bounded: hk_poll waits at most its timeout, and workers wake
-// at least every few milliseconds to notice shutdown.
+// Admission: a batch takes device memory from the server's budget (its work
+// spaces' estimated bytes) and gives it back when it completes; a worker
+// admits as many pending requests as the budget has room for at that
+// moment, at least one when nothing else is in flight, and otherwise waits
+// for memory to free up.
+//
+// Persistent form (hk_server_opts.persistent): the tensor-core scans of all
+// batches in flight -- the bulk of the work, from any registered collection
+// with a 16-bit copy -- run in one resident launch (hk_tc.cu) that takes
+// each batch's scan from a device-resident ring while it runs: a batch
+// admitted while others are on the GPU joins the same launch, and its
+// query blocks interleave with theirs; each query's bound U and candidate
+// lists stay in device memory for the batch's lifetime.  The batches' other
+// steps run on their workers' streams beside it.
+//
+// Every wait is bounded: hk_poll waits at most its timeout, a worker waits at
+// most 120 s for a scan, and workers wake at least every few milliseconds
+// to notice shutdown.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -30,6 +44,7 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kSideSMs = 8;   // SMs the resident scan leaves to the batches' other kernels
 
 struct Request {
     uint64_t ticket;
@@ -59,6 +74,9 @@ struct Worker {
 
 struct hk_server {
     hk_server_opts opts{};
+    hk::TcEngine *engine = nullptr;   // persistent form
+    int64_t budget_used = 0;          // device bytes the batches in flight hold
+    std::condition_variable cv_mem;   // budget freed
     std::vector<hk_index *> colls;
     std::mutex mu;
     std::condition_variable cv_work;   // requests arrived / shutdown
@@ -71,7 +89,7 @@ struct hk_server {
     std::vector<std::unique_ptr<Worker>> workers;
     int device = 0;
     // statistics
-    int64_t batches = 0, served = 0, max_batch_seen = 0, errors = 0;
+    int64_t batches = 0, served = 0, max_batch_seen = 0, errors = 0, budget_peak = 0;
     double busy_s = 0.0;
 };
 
@@ -86,13 +104,21 @@ int64_t bytes_per_query(const hk_index *idx, int k) {
            pool * 8 + 64 * (int64_t)k;
 }
 
+// Device bytes a batch of nq queries with this k holds while in flight
+// (its work space and its retry work space).
+int64_t batch_bytes(const hk_index *idx, int k, int nq) { return bytes_per_query(idx, k) * 2 * nq; }
+
+// Most requests a batch may take now: max_batch, and what the budget has
+// room for beside the batches in flight (at least one when none is).
+// Called with sv->mu held.
 int batch_cap(hk_server *sv, const hk_index *idx, int k) {
     int cap = sv->opts.max_batch > 0 ? sv->opts.max_batch : 1024;
     if (sv->opts.hbm_budget > 0) {
-        const int64_t per = bytes_per_query(idx, k) * 2;   // work space + retry work space
-        const int64_t workers = (int64_t)sv->workers.size();
-        const int64_t fit = sv->opts.hbm_budget / std::max<int64_t>(1, workers) / std::max<int64_t>(1, per);
-        cap = (int)std::max<int64_t>(1, std::min<int64_t>(cap, fit));
+        const int64_t per = std::max<int64_t>(1, batch_bytes(idx, k, 1));
+        const int64_t room = sv->opts.hbm_budget - sv->budget_used;
+        const int64_t fit = room > 0 ? room / per : 0;
+        cap = (int)std::min<int64_t>(cap, fit);
+        if (cap < 1 && sv->budget_used == 0) cap = 1;
     }
     return cap;
 }
@@ -117,6 +143,7 @@ void worker_loop(hk_server *sv, Worker *w) {
     for (;;) {
         std::vector<std::shared_ptr<Request>> batch;
         int coll = -1;
+        int64_t reserved = 0;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             for (;;) {
@@ -146,9 +173,19 @@ void worker_loop(hk_server *sv, Worker *w) {
             int kmax = 0;
             for (auto &r : sv->queues[coll]) kmax = std::max(kmax, r->k);
             const int cap = batch_cap(sv, sv->colls[coll], kmax);
+            if (cap < 1) {
+                // the budget is taken by batches in flight: wait for one to finish
+                sv->cv_mem.wait_for(lk, std::chrono::milliseconds(5));
+                continue;
+            }
             while (!sv->queues[coll].empty() && (int)batch.size() < cap) {
                 batch.push_back(sv->queues[coll].front());
                 sv->queues[coll].pop_front();
+            }
+            if (sv->opts.hbm_budget > 0) {
+                reserved = batch_bytes(sv->colls[coll], kmax, (int)batch.size());
+                sv->budget_used += reserved;
+                sv->budget_peak = std::max(sv->budget_peak, sv->budget_used);
             }
         }
         if (batch.empty()) continue;
@@ -170,6 +207,8 @@ void worker_loop(hk_server *sv, Worker *w) {
             std::memset(&o, 0, sizeof(o));
             o.eapca_th = -1.0f;
             o.sax_th = -1.0f;
+            // graph mode records a pass per index into that index's one graph
+            // work space, which concurrent batches would share: not served
             o.flags = sv->opts.query_flags & ~(uint32_t)(HK_Q_TIMING | HK_Q_GRAPH);
             // the precision form where the collection has it (16-bit copy, n <= 256)
             if ((o.flags & HK_Q_BF16) && (!idx->has_bf16 || idx->n > hk::kTcMaxLen))
@@ -198,6 +237,7 @@ void worker_loop(hk_server *sv, Worker *w) {
                 }
                 r.latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(t1 - r.t_submit).count();
             }
+            sv->budget_used -= reserved;
             sv->batches += 1;
             sv->served += nq;
             sv->max_batch_seen = std::max<int64_t>(sv->max_batch_seen, nq);
@@ -205,6 +245,7 @@ void worker_loop(hk_server *sv, Worker *w) {
             sv->busy_s += std::chrono::duration<double>(t1 - t0).count();
         }
         sv->cv_done.notify_all();
+        sv->cv_mem.notify_all();
     }
 }
 
@@ -222,11 +263,15 @@ int hk_server_create(const hk_server_opts *opts, hk_server **out) {
         if (sv->opts.max_batch < 0 || sv->opts.max_wait_us < 0 || sv->opts.hbm_budget < 0 ||
             sv->opts.workers < 0)
             hk::fail(HK_EINVAL, "negative server option");
-        const int nw = sv->opts.workers > 0 ? sv->opts.workers : 2;
+        if (sv->opts.persistent != 0 && sv->opts.persistent != 1) hk::fail(HK_EINVAL, "persistent must be 0 or 1");
+        const int nw = sv->opts.workers > 0 ? sv->opts.workers : (sv->opts.persistent ? 4 : 2);
         HK_CHECK_CUDA(cudaGetDevice(&sv->device));
+        if (sv->opts.persistent) sv->engine = hk::tc_engine_create(kSideSMs);
         for (int i = 0; i < nw; ++i) {
             auto w = std::make_unique<Worker>();
             HK_CHECK_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+            w->ws.engine = sv->engine;
+            w->ws_retry.engine = sv->engine;
             sv->workers.push_back(std::move(w));
         }
         hk_server *raw = sv.get();
@@ -327,6 +372,15 @@ int hk_server_stats_get(hk_server *sv, hk_server_stats *out) {
     for (auto &q : sv->queues) pending += (int64_t)q.size();
     out->pending = pending;
     out->busy_ns = (int64_t)(sv->busy_s * 1e9);
+    out->budget_peak = sv->budget_peak;
+    if (sv->engine) {
+        hk::TcEngineStats es;
+        hk::tc_engine_stats(sv->engine, &es);
+        out->scan_launches = es.launches;
+        out->scan_jobs = es.jobs;
+        out->scan_jobs_inflight = es.jobs_inflight;
+        out->scan_max_collections = es.max_colls_per_launch;
+    }
     return HK_OK;
 }
 
@@ -346,6 +400,7 @@ int hk_server_destroy(hk_server *sv) {
         if (w->dist_h) cudaFreeHost(w->dist_h);
         if (w->stream) cudaStreamDestroy(w->stream);
     }
+    hk::tc_engine_destroy(sv->engine);
     {
         // requests never served fail with HK_EBUSY
         std::lock_guard<std::mutex> lk(sv->mu);

@@ -62,9 +62,21 @@
 // Three shared-memory stages for series tiles, three TMEM accumulators.  Every
 // mbarrier wait is bounded; on a timeout the CTA raises an error flag,
 // drains, frees its tensor memory and stops.
+//
+// Served form (k_tc_serve): the same roles and pipeline in a resident launch
+// that takes its items from the scans (jobs) of many batches published to a
+// device-resident ring while it runs, each item with its own job's arguments;
+// the host side (TcEngine, at the end of this file) publishes jobs and waits
+// for their completion flags in host-mapped memory.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <memory>
 #include <mutex>
+#include <thread>
+#include <vector>
 
 #include "hk_device.cuh"
 #include "hk_internal.cuh"
@@ -310,6 +322,129 @@ __device__ void fetch_item(const TcArgs &A, int64_t total, TcItem &D, int lane) 
     const int32_t *lq = A.leaf_q + qoff + grp * kTcM;
     for (int g = lane; g < kTcM; g += 32) D.qid[g] = g < gq ? lq[g] : -1;
     __syncwarp();
+}
+
+
+// Shared state of the served kernel: the batch kernel's, plus its current job.
+struct TcServeShared : TcShared {
+    TcArgs job_args;
+    int64_t job_total;
+    int job_slot;
+    uint32_t job_seq;
+    int quit;
+};
+
+// Describe work item `it` in D (one warp).  The leaf is the last l with
+// item_off[l] <= it, found by a 32-way search (three rounds of one coalesced
+// probe each for ~2,000 leaves).
+__device__ void describe_item(const TcArgs &A, int64_t it, TcItem &D, int lane) {
+    if (lane == 0) D.it = it;
+    int lo = 0, hi = (int)A.L;   // item_off[lo] <= it < item_off[hi + 1]
+    while (hi - lo > 31) {
+        const int64_t span = hi - lo;
+        const int pos = lo + (int)(span * (lane + 1) / 32);
+        const unsigned m = __ballot_sync(0xffffffffu, A.item_off[pos] <= it);
+        const int last = m ? 31 - __clz((int)m) : -1;
+        const int nlo = last >= 0 ? lo + (int)(span * (last + 1) / 32) : lo;
+        const int nhi = last < 31 ? lo + (int)(span * (last + 2) / 32) - 1 : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    {
+        const int pos = lo + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, pos <= hi && A.item_off[pos] <= it);
+        lo += 31 - __clz((int)m);
+    }
+    const int leaf = lo;
+    const int64_t local = it - A.item_off[leaf];
+    const int qoff = A.leaf_qoff[leaf];
+    const int nql = A.leaf_qoff[leaf + 1] - qoff;
+    const int ngroups = (nql + kTcM - 1) / kTcM;
+    const int64_t tile = local / ngroups;
+    const int grp = (int)(local % ngroups);
+    const int gq = min(kTcM, nql - grp * kTcM);
+    if (lane == 0) {
+        const int64_t lo_s = A.leaf_off[leaf], hi_s = A.leaf_off[leaf + 1];
+        D.s0 = lo_s + tile * A.S_T;
+        D.s1 = min(D.s0 + (int64_t)A.S_T, hi_s);
+        D.base = D.s0 & ~(int64_t)7;
+        D.tiles = (int)((D.s1 - D.base + kTcN - 1) / kTcN);
+        D.gq = gq;
+    }
+    const int32_t *lq = A.leaf_q + qoff + grp * kTcM;
+    for (int g = lane; g < kTcM; g += 32) D.qid[g] = g < gq ? lq[g] : -1;
+    __syncwarp();
+}
+
+// Served form (one warp): claim the next item of the oldest published job
+// that has items left, copy that job's arguments into shared memory and
+// describe the item.  A claim is one compare-and-swap on the ring's word
+// (job sequence, next item), so an item is claimed once, and only while its
+// job is the current one (a ring slot is rewritten only after its job
+// completed).  Sets S.quit when no job came for V.idle_ns.
+__device__ void serve_fetch(const TcServe &V, TcServeShared &S, int lane) {
+    int slot = -1;
+    long long item = 0;
+    uint32_t seq = 0;
+    if (lane == 0) {
+        uint64_t idle0 = 0;
+        for (;;) {
+            const unsigned long long w = atomicAdd(V.word, 0ull);
+            const uint32_t cur = (uint32_t)(w >> 32), i = (uint32_t)w;
+            if (cur == *V.published) {   // nothing published beyond the current job
+                const uint64_t now = global_ns();
+                if (idle0 == 0) {
+                    idle0 = now;
+                } else if (now - idle0 > V.idle_ns) {
+                    break;
+                }
+                __nanosleep(2000);
+                continue;
+            }
+            idle0 = 0;
+            const int sl = (int)(cur % kTcRing);
+            const long long total = __ldcg(&V.jobs[sl].total);
+            const unsigned long long nw =
+                (long long)i < total ? w + 1 : ((unsigned long long)(cur + 1) << 32);
+            if (atomicCAS(V.word, w, nw) == w && (long long)i < total) {
+                slot = sl;
+                item = i;
+                seq = cur;
+                break;
+            }
+        }
+    }
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    seq = __shfl_sync(0xffffffffu, seq, 0);
+    if (slot < 0) {
+        if (lane == 0) S.quit = 1;
+        __syncwarp();
+        return;
+    }
+    // the job's arguments, read past L1 (the slot's earlier contents may sit there)
+    const int words = (int)(sizeof(TcArgs) / 4);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&V.jobs[slot].args);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&S.job_args);
+    for (int j = lane; j < words; j += 32) dst[j] = __ldcg(src + j);
+    if (lane == 0) {
+        S.job_total = __ldcg(&V.jobs[slot].total);
+        S.job_slot = slot;
+        S.job_seq = seq;
+    }
+    __syncwarp();
+    describe_item(S.job_args, item, S.item, lane);
+}
+
+// Served form: one item of the current job done (thread 0, after the CTA
+// finished it); the job's last item publishes its completion to the host.
+__device__ void serve_done(const TcServe &V, const TcServeShared &S) {
+    __threadfence();
+    const int32_t d = atomicAdd(&V.done[S.job_slot], 1) + 1;
+    if ((int64_t)d == S.job_total) {
+        __threadfence_system();
+        V.done_seq[S.job_slot] = S.job_seq;
+    }
 }
 
 }  // namespace
@@ -615,6 +750,323 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
     }
 }
 
+// The served form of k_tc_scan: the same roles and pipeline, with items taken
+// from the jobs of a ring (V) until none comes for V.idle_ns; each item's
+// arguments are its job's (copied into shared memory).  The batch kernel is
+// kept as its own function so its code stays exactly as measured.
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_serve(TcServe V) {
+    constexpr bool kHooks = false, kServe = true;
+    const TcArgs P{};
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    const int nst = kTcStages;
+    unsigned char *sB = tc_smem;                             // 1024-aligned stages
+    float2 *sX = reinterpret_cast<float2 *>(sB + kTcStages * kTcStageBytes);  // kNormSlots * kTcN
+    float *kbest = reinterpret_cast<float *>(sX + kNormSlots * kTcN);      // kTcEpiThreads * kLocalK
+    TcServeShared &S = *reinterpret_cast<TcServeShared *>(kbest + kTcEpiThreads * kLocalK);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        for (int b = 0; b < kAcc; ++b) {
+            mbar_init(&S.acc_full[b], 1);
+            mbar_init(&S.acc_empty[b], 32 * kTcEpiWarps);
+        }
+        mbar_init(&S.never, 1);
+        S.abort_flag = 0;
+        S.quit = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {   // the MMA warp owns the tensor memory
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const TcArgs &A = kServe ? S.job_args : P;   // the current item's arguments
+    int64_t total = 0;
+    if constexpr (!kServe) total = P.item_off[P.L];
+
+    // running counts of barrier completions (phases), kept per role
+    uint32_t g_tile = 0;   // tiles processed by this CTA so far (all roles agree)
+    uint32_t issued = 0;   // producer: tiles whose copies it issued; MMA warp: tiles it committed
+    const uint64_t wait_ns = (kHooks && P.wait_ns) ? P.wait_ns : kWaitNs;
+    long long my_cand = 0, my_pairs = 0, my_bytes = 0;
+
+    // Items are claimed when a CTA is ready for one, so the query blocks of
+    // a leaf range start together and share its tiles in L2.
+    for (;;) {
+        if (warp == 0) {
+            if constexpr (kServe)
+                serve_fetch(V, S, lane);
+            else
+                fetch_item(P, total, S.item, lane);
+        }
+        __syncthreads();
+        const TcItem &D = S.item;
+        if constexpr (kServe) {
+            if (S.quit || S.abort_flag) break;
+        } else {
+            if (D.it >= total || S.abort_flag) break;
+        }
+        const int n = A.n;
+        const uint32_t b_bytes = (uint32_t)kTcN * n * 2;             // a whole tile
+        const uint32_t lbo = 128, sbo = (uint32_t)(n / 8) * 128;   // series tile, K-major core matrices
+        // the query block into tensor memory: epilogue warp w writes lane
+        // quarter w%4, 32-column chunks c (points 64c..64c+63) of its column
+        // group (w-2)/4; zeros past gq and past n
+        if (warp >= 2) {
+            const int r = (warp & 3) * 32 + lane;
+            const int q = D.qid[r];
+#pragma unroll 1
+            for (int h = 0; h < kEpiChunks; ++h) {
+                const int c = ((warp - 2) >> 2) * kEpiChunks + h;
+                if (64 * c >= n) break;
+                uint32_t w[32];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    const int k0 = 64 * c + 8 * i;
+                    if (q >= 0 && k0 < n) v = *reinterpret_cast<const uint4 *>(A.Qb + (int64_t)q * n + k0);
+                    w[4 * i + 0] = v.x;
+                    w[4 * i + 1] = v.y;
+                    w[4 * i + 2] = v.z;
+                    w[4 * i + 3] = v.w;
+                }
+                tmem_st32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(kTmemA + 32 * c), w);
+            }
+            tmem_wait_st();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const int T = D.tiles;
+        const int64_t base = D.base, s0 = D.s0, s1 = D.s1;
+        if (tid == 0) my_bytes += (long long)T * (b_bytes + kTcN * (long long)sizeof(float2));
+
+        if (warp == 0) {
+            // ---------------- producer: one bulk copy per tile, plus its norms
+            if (lane == 0) {
+                for (int t = 0; t < T; ++t) {
+                    const uint32_t gt = g_tile + t;
+                    const int s = gt % nst;
+                    const uint32_t use = gt / nst;
+                    if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1, &S.abort_flag, wait_ns)) break;
+                    const int64_t row0 = base + (int64_t)t * kTcN;
+                    const uint32_t norm_bytes = kTcN * (uint32_t)sizeof(float2);
+                    mbar_arrive_expect_tx(&S.full[s], b_bytes + norm_bytes);
+                    bulk_g2s(sB + s * kTcStageBytes, A.Xb + row0 * n, b_bytes, &S.full[s]);
+                    bulk_g2s(sX + (gt % kNormSlots) * kTcN, A.xq + row0, norm_bytes, &S.full[s]);
+                    issued = gt + 1;
+                }
+            }
+        } else if (warp == 1) {
+            // ---------------- MMA issuer
+            if (lane == 0) {
+                const uint32_t a_tmem = tmem + (uint32_t)kTmemA;
+                const int ksteps = n / 16;
+                for (int t = 0; t < T; ++t) {
+                    const uint32_t gt = g_tile + t;
+                    const int s = gt % nst;
+                    const uint32_t use = gt / nst;
+                    const int b = gt % kAcc;
+                    const uint32_t ause = gt / kAcc;
+                    if (ause > 0 && !mbar_wait(&S.acc_empty[b], (ause - 1) & 1, &S.abort_flag, wait_ns)) break;
+                    if (!mbar_wait(&S.full[s], use & 1, &S.abort_flag, wait_ns)) break;
+                    tc_fence_after();
+                    const uint32_t b_base = smem_u32(sB + s * kTcStageBytes);
+                    const uint32_t d = tmem + (uint32_t)(b * kTcN);
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        // K step: 16 points = 8 columns of A, 2 core matrices of B
+                        const uint64_t bd = smem_desc(b_base + ks * 2 * 128, lbo, sbo);
+                        mma_ts(d, a_tmem + (uint32_t)(ks * 8), bd, A.idesc, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&S.empty[s]);
+                    mma_commit(&S.acc_full[b]);
+                    issued = gt + 1;
+                }
+            }
+        } else {
+            // ---------------- epilogue: thread owns query row r, a quarter of the columns
+            const int r = (warp & 3) * 32 + lane;   // TMEM lane quarter of this warp
+            const int cq = (warp - 2) >> 2;         // column group
+            const int q = D.qid[r];
+            float q2e = 0.f, qa = 0.f, qoff2 = 0.f, U = 0.f;
+            if (q >= 0) {
+                q2e = A.q2e[q];
+                qa = A.qa[q];
+                qoff2 = A.qoff2[q];
+                U = __uint_as_float(A.U[q]);
+            }
+            // the k best upper bounds of this thread: slot i of epilogue thread
+            // e at kbest[i * kTcEpiThreads + e] (conflict-free); the column
+            // quarters of a row keep separate lists
+            float *kb = kbest + (tid - 64);
+            const int kl = (A.k <= kLocalK) ? A.k : 0;
+            for (int i = 0; i < kl; ++i) kb[i * kTcEpiThreads] = INFINITY;
+            float kth = INFINITY;      // k-th smallest upper bound seen by this thread
+            long long pairs = 0;
+            // test hook: one epilogue warp waits for a barrier nothing
+            // arrives at, so its bounded wait runs out and the CTA aborts
+            const bool stalled = kHooks && P.dbg_stall && warp == 2 && g_tile == 0 &&
+                                 !mbar_wait_warp(&S.never, 0, &S.abort_flag, wait_ns);
+            for (int t = 0; t < T && !stalled; ++t) {
+                const uint32_t gt = g_tile + t;
+                const int b = gt % kAcc;
+                const uint32_t ause = gt / kAcc;
+                if (!mbar_wait_warp(&S.acc_full[b], ause & 1, &S.abort_flag, wait_ns)) break;
+                tc_fence_after();
+                if (q >= 0 && (t & 7) == 0) U = fminf(U, __uint_as_float(A.U[q]));
+                const int64_t row0 = base + (int64_t)t * kTcN;
+                // columns of this tile inside [s0, s1)
+                const int jlo = (int)max((int64_t)0, s0 - row0);
+                const int jhi = (int)min((int64_t)kTcN, s1 - row0);
+                const float thr = U - q2e;   // lo <= U  <=>  x2e - qa|x| - 2v <= U - q2e
+                const float2 *xs = sX + (gt % kNormSlots) * kTcN;
+                uint32_t raw[kEpiChunks][32];
+#pragma unroll
+                for (int h = 0; h < kEpiChunks; ++h)
+                    tmem_ld32_issue(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                        (uint32_t)(b * kTcN + (cq * kEpiChunks + h) * 32),
+                                    raw[h]);
+                tmem_wait_ld();
+                // the accumulator is in registers: release it to the MMAs
+                // before filtering
+                tc_fence_before();
+                mbar_arrive(&S.acc_empty[b]);
+#pragma unroll
+                for (int h = 0; h < kEpiChunks; ++h) {
+                const int cb = (cq * kEpiChunks + h) * 32;
+                // columns of this thread inside [s0, s1)
+                const int a = max(jlo - cb, 0), z = min(jhi - cb, 32);
+                if (q >= 0 && a < z) {
+                    pairs += z - a;
+                    // the filter value of every column, reduced to its minimum:
+                    // a column survives iff its value is <= thr, so a minimum
+                    // above thr (the common case) clears all 32 at once
+                    float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 x01 = *reinterpret_cast<const float4 *>(xs + cb + j);
+                        const float4 x23 = *reinterpret_cast<const float4 *>(xs + cb + j + 2);
+                        m0 = fminf(m0, fmaf(-2.0f, __uint_as_float(raw[h][j + 0]), fmaf(-qa, x01.y, x01.x)));
+                        m1 = fminf(m1, fmaf(-2.0f, __uint_as_float(raw[h][j + 1]), fmaf(-qa, x01.w, x01.z)));
+                        m2 = fminf(m2, fmaf(-2.0f, __uint_as_float(raw[h][j + 2]), fmaf(-qa, x23.y, x23.x)));
+                        m3 = fminf(m3, fmaf(-2.0f, __uint_as_float(raw[h][j + 3]), fmaf(-qa, x23.w, x23.z)));
+                    }
+                    const bool any = fminf(fminf(m0, m1), fminf(m2, m3)) <= thr;
+                    if (any || A.dbg_lo) {
+                        const uint32_t valid =
+                            (z >= 32 ? 0xffffffffu : ((1u << z) - 1u)) & ~((1u << a) - 1u);
+                        float v[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[h][j]);
+                        uint32_t hit = 0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float2 xv = xs[cb + j];
+                            const float lhs = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x));
+                            hit |= (lhs <= thr ? 1u : 0u) << j;
+                        }
+                        hit &= valid;
+                        if (A.dbg_lo) {
+                            for (int j = a; j < z; ++j) {
+                                const float2 xv = xs[cb + j];
+                                const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
+                                const float bs = lo + 2.0f * qa * xv.y;
+                                A.dbg_lo[(int64_t)q * A.N + row0 + cb + j] = lo;
+                                A.dbg_up[(int64_t)q * A.N + row0 + cb + j] =
+                                    bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
+                            }
+                        }
+                        while (hit) {
+                            // survivor: exact lower / upper bounds in the
+                            // certified form (rounded outward)
+                            const int j = __ffs(hit) - 1;
+                            hit &= hit - 1;
+                            const float2 xv = xs[cb + j];
+                            const float lo = fmaf(-2.0f, v[j], fmaf(-qa, xv.y, xv.x)) + q2e;
+                            const float bs = lo + 2.0f * qa * xv.y;
+                            const float up = bs + fabsf(bs) * 0x1p-18f + A.eb2 * (q2e + xv.x) + qoff2;
+                            if (kl && up < kth) {
+                                int mi = 0;
+                                for (int i = 1; i < kl; ++i)
+                                    if (kb[i * kTcEpiThreads] > kb[mi * kTcEpiThreads]) mi = i;
+                                kb[mi * kTcEpiThreads] = up;
+                                float mx = kb[0];
+                                for (int i = 1; i < kl; ++i) mx = fmaxf(mx, kb[i * kTcEpiThreads]);
+                                kth = mx;
+                            }
+                            if (lo <= U) {
+                                const int slot = atomicAdd(&A.cand_cnt[q], 1);
+                                if (slot < A.cand_C) {
+                                    A.cand_p[(int64_t)q * A.cand_C + slot] = (int32_t)(row0 + cb + j);
+                                    A.cand_lb[(int64_t)q * A.cand_C + slot] = lo;
+                                    ++my_cand;
+                                } else {
+                                    atomicOr(&A.qflag[q], 1);
+                                }
+                            }
+                        }
+                    }
+                }
+                }
+                if (q >= 0 && kth < U) {
+                    U = kth;
+                    atomicMin(&A.U[q], __float_as_uint(kth));
+                }
+            }
+            my_pairs += pairs;
+        }
+        g_tile += T;
+        __syncthreads();
+        if constexpr (kServe) {
+            if (tid == 0 && !S.abort_flag) serve_done(V, S);
+        }
+    }
+    // drain: a CTA that aborted may have copies or MMAs in flight.  The
+    // producer waits for the copies of the last kTcStages tiles it issued
+    // (earlier ones were consumed by the MMA warp, so they landed); the MMA
+    // warp waits for the commits of the last tile it issued (a commit
+    // arrives once every earlier MMA of the thread completed).  Each wait
+    // ends by a deadline; then the tensor memory is freed.
+    if (S.abort_flag) {
+        if (tid == 0) atomicOr(A.err, 2);
+        const uint64_t deadline = global_ns() + kDrainNs;
+        bool landed = true;
+        if (warp == 0 && lane == 0) {
+            for (uint32_t gt = issued > (uint32_t)nst ? issued - nst : 0; gt < issued; ++gt)
+                landed &= mbar_wait_until(&S.full[gt % nst], (gt / nst) & 1, deadline);
+        } else if (warp == 1 && lane == 0 && issued > 0) {
+            const uint32_t last = issued - 1;
+            landed &= mbar_wait_until(&S.empty[last % nst], (last / nst) & 1, deadline);
+            landed &= mbar_wait_until(&S.acc_full[last % kAcc], (last / kAcc) & 1, deadline);
+        }
+        if (!landed) atomicOr(A.err, 4);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    }
+    my_pairs = warp_sum_ll(my_pairs);
+    my_cand = warp_sum_ll(my_cand);
+    if (lane == 0 && P.stats) {
+        stat_add(&P.stats[P.stat_pairs], my_pairs);
+        stat_add(&P.stats[P.stat_cands], my_cand);
+        if (tid == 0) stat_add(&P.stats[P.stat_bytes], my_bytes);
+    }
+}
+
 // 16-bit copy (bfloat16 or float16) of the leaf-ordered collection in
 // core-matrix order, and per series {|x|^2 (1 - eb) rounded down, |x|
 // rounded up} from binary64 sums.  Values a float16 cannot hold set *bad.
@@ -795,6 +1247,11 @@ __global__ void k_tc_rescore(const float *__restrict__ Q, const float *__restric
     if (lane == 0 && done) stat_add(&stats[stat_slot], done);
 }
 
+size_t tc_serve_smem_bytes() {
+    return (size_t)kTcStages * kTcStageBytes + (size_t)kNormSlots * kTcN * 8 +
+           (size_t)kTcEpiThreads * kLocalK * 4 + sizeof(TcServeShared) + 1024;
+}
+
 size_t tc_smem_bytes(int n) {
     (void)n;   // stages are sized for the longest series
     return (size_t)kTcStages * kTcStageBytes + (size_t)kNormSlots * kTcN * 8 +
@@ -838,6 +1295,170 @@ void launch_tc_scan(const TcArgs &a, cudaStream_t s) {
     else
         k_tc_scan<false><<<sms, kTcThreads, smem, s>>>(a);
     HK_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------- served form (host)
+// One resident launch of the served scan takes the scans (jobs) of all
+// batches in flight, from any collection with a 16-bit copy: a job's
+// arguments go to a ring slot in device memory, then the count of
+// published jobs (host-mapped memory, read by the launch) moves on; the
+// launch writes each finished job's sequence number back to host-mapped
+// memory.  A launch leaves after idle_ns without work; a job published
+// after it left starts another.  Every wait is bounded.
+struct TcEngine {
+    int ctas = 0;
+    cudaStream_t stream = nullptr;   // the resident launch
+    cudaStream_t pub = nullptr;      // the ring's copies
+    DevBuf<TcJob> jobs;
+    DevBuf<unsigned long long> word;
+    DevBuf<int32_t> done;
+    uint32_t *ctl_h = nullptr;       // mapped: [0] published, [1 + slot] last completed sequence
+    uint32_t *ctl_d = nullptr;
+    uint32_t published = 0;
+    bool launched = false;
+    cudaEvent_t ev = nullptr;        // recorded after the last launch
+    std::mutex mu;
+    TcEngineStats st{};
+    std::vector<const void *> colls;   // collections the current launch took jobs of
+    uint64_t idle_ns = 2000000;
+};
+
+namespace {
+
+bool engine_running(TcEngine *e) {
+    if (!e->launched) return false;
+    const cudaError_t r = cudaEventQuery(e->ev);
+    if (r == cudaErrorNotReady) return true;
+    HK_CHECK_CUDA(r);
+    return false;
+}
+
+void engine_launch(TcEngine *e) {
+    TcServe V{};
+    V.jobs = e->jobs.p;
+    V.word = e->word.p;
+    V.done = e->done.p;
+    V.published = e->ctl_d;
+    V.done_seq = e->ctl_d + 1;
+    V.idle_ns = e->idle_ns;
+    k_tc_serve<<<e->ctas, kTcThreads, tc_serve_smem_bytes(), e->stream>>>(V);
+    HK_CHECK_LAUNCH();
+    HK_CHECK_CUDA(cudaEventRecord(e->ev, e->stream));
+    e->launched = true;
+    e->st.launches += 1;
+    e->colls.clear();
+}
+
+void engine_note_coll(TcEngine *e, const void *x) {
+    if (std::find(e->colls.begin(), e->colls.end(), x) == e->colls.end()) e->colls.push_back(x);
+    e->st.max_colls_per_launch = std::max<long long>(e->st.max_colls_per_launch, (long long)e->colls.size());
+}
+
+}  // namespace
+
+TcEngine *tc_engine_create(int spare_sms) {
+    std::unique_ptr<TcEngine> e(new TcEngine());
+    int dev = 0, sms = 0;
+    HK_CHECK_CUDA(cudaGetDevice(&dev));
+    HK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // a few SMs stay free for the batches' other kernels, which cannot share
+    // an SM with the resident launch's shared memory
+    e->ctas = std::max(1, sms - spare_sms);
+    HK_CHECK_CUDA(cudaFuncSetAttribute(k_tc_serve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_serve_smem_bytes()));
+    HK_CHECK_CUDA(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+    HK_CHECK_CUDA(cudaStreamCreateWithFlags(&e->pub, cudaStreamNonBlocking));
+    HK_CHECK_CUDA(cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming));
+    e->jobs.alloc(kTcRing, e->pub);
+    e->word.alloc(1, e->pub);
+    e->done.alloc(kTcRing, e->pub);
+    HK_CHECK_CUDA(cudaMemsetAsync(e->word.p, 0, sizeof(unsigned long long), e->pub));
+    HK_CHECK_CUDA(cudaMemsetAsync(e->done.p, 0, kTcRing * sizeof(int32_t), e->pub));
+    HK_CHECK_CUDA(cudaHostAlloc((void **)&e->ctl_h, (1 + kTcRing) * sizeof(uint32_t), cudaHostAllocMapped));
+    e->ctl_h[0] = 0;
+    for (int i = 0; i < kTcRing; ++i) e->ctl_h[1 + i] = 0xffffffffu;
+    HK_CHECK_CUDA(cudaHostGetDevicePointer((void **)&e->ctl_d, e->ctl_h, 0));
+    HK_CHECK_CUDA(cudaStreamSynchronize(e->pub));
+    return e.release();
+}
+
+void tc_engine_destroy(TcEngine *e) {
+    if (!e) return;
+    // the launch leaves by itself once idle (bounded)
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->pub) cudaStreamSynchronize(e->pub);
+    if (e->ev) cudaEventDestroy(e->ev);
+    if (e->stream) cudaStreamDestroy(e->stream);
+    if (e->pub) cudaStreamDestroy(e->pub);
+    if (e->ctl_h) cudaFreeHost(e->ctl_h);
+    delete e;
+}
+
+void tc_engine_stats(TcEngine *e, TcEngineStats *out) {
+    std::lock_guard<std::mutex> lk(e->mu);
+    *out = e->st;
+}
+
+void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout_ns) {
+    using clock = std::chrono::steady_clock;
+    const auto t0 = clock::now();
+    auto late = [&] {
+        return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - t0).count() >
+               timeout_ns;
+    };
+    volatile uint32_t *done_seq = e->ctl_h + 1;
+    uint32_t seq;
+    int slot;
+    {
+        std::unique_lock<std::mutex> lk(e->mu);
+        seq = e->published;
+        slot = (int)(seq % kTcRing);
+        // the slot's previous job must have completed before it is rewritten
+        while (seq >= (uint32_t)kTcRing && done_seq[slot] != seq - kTcRing) {
+            if (late()) fail(HK_ETIMEOUT, "served scan: ring slot %d still busy", slot);
+            if (!engine_running(e)) engine_launch(e);
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        }
+        TcJob j{};
+        j.args = a;
+        j.args.stats = nullptr;      // per-launch counters do not apply to a shared launch
+        j.args.work_ctr = nullptr;
+        j.total = items;
+        j.seq = seq;
+        HK_CHECK_CUDA(cudaMemcpyAsync(e->jobs.p + slot, &j, sizeof(j), cudaMemcpyHostToDevice, e->pub));
+        HK_CHECK_CUDA(cudaMemsetAsync(e->done.p + slot, 0, sizeof(int32_t), e->pub));
+        HK_CHECK_CUDA(cudaStreamSynchronize(e->pub));
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        e->published = seq + 1;
+        *(volatile uint32_t *)e->ctl_h = seq + 1;
+        e->st.jobs += 1;
+        if (engine_running(e)) {
+            e->st.jobs_inflight += 1;
+        } else {
+            engine_launch(e);
+        }
+        engine_note_coll(e, a.Xb);
+    }
+    for (;;) {
+        if (done_seq[slot] == seq) break;
+        if (late()) fail(HK_ETIMEOUT, "served scan: job %u not finished in time", seq);
+        if (!engine_running(e)) {
+            std::lock_guard<std::mutex> lk(e->mu);
+            if (done_seq[slot] != seq && !engine_running(e)) {
+                // the launch left without finishing this job: an aborted CTA
+                // (a bounded wait ran out) leaves its error word set
+                int32_t err = 0;
+                HK_CHECK_CUDA(cudaMemcpyAsync(&err, a.err, sizeof(int32_t), cudaMemcpyDeviceToHost, e->pub));
+                HK_CHECK_CUDA(cudaStreamSynchronize(e->pub));
+                if (err) fail(HK_ETIMEOUT, "served scan: a bounded wait ran out (flag %d)", err);
+                engine_launch(e);   // it went idle before this job was published
+            }
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(10));
+    }
+    std::atomic_thread_fence(std::memory_order_seq_cst);
 }
 
 double tc_abs_unit(int fmt) {

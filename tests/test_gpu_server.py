@@ -122,3 +122,74 @@ def test_server_rejects_bad_requests(hb, two_collections):
     with pytest.raises(hb.HerculesError):
         sv.poll(987654, 1, timeout_us=10)
     sv.close()
+
+
+def test_persistent_scan_admits_batches_midflight(hb, oracle_lib):
+    """Persistent form: requests for three collections of different series
+    lengths (64, 128, 256; float16 copies) arrive in waves while earlier
+    batches are on the GPU; their tensor-core scans run as jobs of resident
+    launches, batches admitted mid-flight joining a running launch and
+    several collections sharing one.  Every answer equals the same query's
+    answer alone (hk_query) and the oracle's."""
+    import time
+    from paper_2212_13297_gb300 import workload as wl
+    Xs = [wl.random_walk(40_000, 64, seed=111, device="cuda"),
+          wl.gaussian(30_000, 128, seed=112, device="cuda", l2=True),
+          wl.random_walk(30_000, 256, seed=113, device="cuda")]
+    norms = ["z", "l2", "z"]
+    idxs = [hb.Index(X, 400, flags=hb.HK_BUILD_FP16) for X in Xs]
+    Qs = [wl.queries(X, 90, [0.05, 0.5, 1.0], seed=114 + i, norm=norms[i])[0].cpu().numpy()
+          for i, X in enumerate(Xs)]
+    sv = hb.Server(max_batch=24, query_flags=hb.HK_Q_BF16, workers=4, persistent=1)
+    colls = [sv.add(ix) for ix in idxs]
+    rng = np.random.default_rng(9)
+    reqs = [(c, i, int(rng.choice([1, 10, 50]))) for c in range(3) for i in range(90)]
+    rng.shuffle(reqs)
+    tickets = []
+    for w0 in range(0, len(reqs), 45):          # six waves, a few ms apart
+        for c, i, k in reqs[w0:w0 + 45]:
+            tickets.append(sv.submit(colls[c], Qs[c][i], k))
+        time.sleep(0.004)
+    got = []
+    for t, (c, i, k) in zip(tickets, reqs):
+        r = sv.poll(t, k, timeout_us=60_000_000)
+        assert r is not None
+        got.append(r)
+    st = sv.stats()
+    sv.close()
+    assert st["errors"] == 0 and st["served"] == len(reqs)
+    assert st["scan_jobs"] >= st["batches"] > 0
+    assert st["scan_launches"] < st["scan_jobs"]        # launches took several batches' scans
+    assert st["scan_jobs_inflight"] > 0                # scans admitted while a launch ran
+    assert st["scan_max_collections"] >= 2             # collections of different n in one launch
+    for (c, i, k), r in zip(reqs, got):
+        ids, dist, _ = idxs[c].query(Qs[c][i:i + 1], k, flags=hb.HK_Q_BF16)
+        np.testing.assert_array_equal(r[0], ids[0])
+        np.testing.assert_array_equal(r[1], dist[0])
+    for c in range(3):
+        sel = [j for j, rq in enumerate(reqs) if rq[0] == c][:20]
+        qs = np.stack([Qs[c][reqs[j][1]] for j in sel])
+        oids, _ = oracle.knn(Xs[c].cpu().numpy(), qs, 50)
+        for row, j in enumerate(sel):
+            k = reqs[j][2]
+            np.testing.assert_array_equal(got[j][0], oids[row, :k])
+
+
+def test_budget_admits_as_memory_frees(hb, two_collections):
+    """A device budget that holds only a few queries' work spaces: workers
+    admit what fits beside the batches in flight and wait for memory to free
+    up; every request is answered and the budget is never exceeded."""
+    c = two_collections
+    budget = 96 << 20
+    sv = hb.Server(max_batch=256, hbm_budget=budget, workers=3)
+    coll = sv.add(c["idx"][0])
+    ts = [sv.submit(coll, c["Q"][0][i % 120], 3) for i in range(150)]
+    for i, t in enumerate(ts):
+        ids, _, _ = sv.poll(t, 3, timeout_us=60_000_000)
+        ref, _, _ = c["idx"][0].query(c["Q"][0][(i % 120):(i % 120) + 1], 3)
+        np.testing.assert_array_equal(ids, ref[0])
+    st = sv.stats()
+    sv.close()
+    assert st["errors"] == 0 and st["served"] == 150
+    assert 0 < st["budget_peak"] <= budget
+    assert st["max_batch"] < 150
