@@ -254,7 +254,7 @@ def serve(binding, idx, Q_all, k, max_batch, qflags, rate, seconds, form, persis
     n_req = max(1, int(rate * seconds))
     gaps = rng.exponential(1.0 / rate, n_req)
     sv = binding.Server(max_batch=max_batch, max_wait_us=0, query_flags=qflags,
-                        workers=4 if persistent else 2, persistent=persistent)
+                        workers=3 if persistent else 2, persistent=persistent)
     coll = sv.add(idx)
     # warm the workers' buffers
     for t in [sv.submit(coll, Qh[i], k) for i in range(min(64, len(Qh)))]:
@@ -295,7 +295,7 @@ def serve(binding, idx, Q_all, k, max_batch, qflags, rate, seconds, form, persis
     sv.close()
     ls = np.sort(lat)
     return dict(kind="open loop, Poisson arrivals, one query per request, %s" % (
-                    "persistent scan, 4 workers" if persistent else "batch-level, 2 workers"), form=form,
+                    "persistent scan, 3 workers" if persistent else "batch-level, 2 workers"), form=form,
                 scan_launches=st["scan_launches"], scan_jobs=st["scan_jobs"],
                 scan_jobs_inflight=st["scan_jobs_inflight"],
                 offered_rate=rate, requests=n_req, answered_per_s=n_req / wall,
@@ -336,7 +336,7 @@ def serve_mix(args):
         torch.cuda.empty_cache()
         builds.append(time.perf_counter() - t0)
     sv = binding.Server(max_batch=1024, max_wait_us=0, query_flags=sv_flags,
-                        workers=4 if args.persistent else 2, persistent=1 if args.persistent else 0)
+                        workers=3 if args.persistent else 2, persistent=1 if args.persistent else 0)
     colls = [sv.add(ix) for ix in idxs]
     for ci in range(len(MIX)):   # warm each collection's path
         for t in [sv.submit(colls[ci], pools[ci][i], kk) for i, kk in enumerate((1, 10, 100))]:
@@ -398,7 +398,7 @@ def serve_mix(args):
                 scan_jobs_inflight=st["scan_jobs_inflight"], scan_max_collections=st["scan_max_collections"],
                 config=dict(workload="served mix: " + "; ".join(m[0] for m in MIX), k=[1, 10, 100],
                             sigma="uniform [0.01, 1.0]", arrivals="Poisson, seed 2",
-                            server="persistent scan, 4 workers" if args.persistent else "batch-level, 2 workers"))
+                            server="persistent scan, 3 workers" if args.persistent else "batch-level, 2 workers"))
     print(json.dumps(line), flush=True)
 
 
@@ -797,26 +797,37 @@ def main():
     alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
 
     def plain_roof(a):
+        """The float32 scan: FP32 ALU rate on its (q-x)^2 points (what bounds it:
+        it is issue-bound), the rate of its algorithmic scan bytes (per work
+        item; L2 serves the query groups' repeats, so not an HBM figure), and
+        DRAM GB/s from a capture's DRAM-to-algorithmic ratio when one exists
+        for this kernel source."""
         scan_s = a["scan_ns"] / 1e9
         alu_ach = 3.0 * a["points_computed"] / scan_s / 1e12 if scan_s else None
-        hbm_ach = a["scan_bytes"] / scan_s / 1e9 if scan_s else None
+        rate = a["scan_bytes"] / scan_s / 1e9 if scan_s else None
+        tr = traffic_ratio("k_scan", "plain")
+        dram = None
+        if tr and rate:
+            dram = dict(achieved=tr["exact"] * rate, peak=pk["hbm_gbs"], unit="GB/s",
+                        frac=tr["exact"] * rate / pk["hbm_gbs"],
+                        note="DRAM bytes = %.3f x the algorithmic scan bytes (ncu capture of %s)" % (
+                            tr["exact"], tr["capture"]))
         return dict(kernel="k_scan", alu=dict(achieved=alu_ach, peak=alu_peak, unit="TFLOP/s",
                                               frac=(alu_ach or 0) / alu_peak),
-                    hbm=dict(achieved=hbm_ach, peak=pk["hbm_gbs"], unit="GB/s",
-                             frac=(hbm_ach or 0) / pk["hbm_gbs"]),
-                    share_of_step=None)
+                    scan_byte_rate=dict(achieved=rate, unit="GB/s",
+                                        note="16 B per iSAX word + 64 B per 16-point chunk, counted per work "
+                                             "item (query group); L2 serves the groups' repeats"),
+                    dram=dram, share_of_step=None)
 
     if args.form == "plain":
         pr = plain_roof(agg_ins)
-        if pr["alu"]["frac"] >= pr["hbm"]["frac"]:
-            roof = dict(bound="alu", achieved=pr["alu"]["achieved"], peak=alu_peak, unit="TFLOP/s",
-                        frac=pr["alu"]["frac"], traffic=None, kernel="k_scan",
-                        peak_note="derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz; "
-                                  "3 flops per (q-x)^2 point" % pk["sm_max_mhz"])
-        else:
-            roof = dict(bound="hbm", achieved=pr["hbm"]["achieved"], peak=pk["hbm_gbs"], unit="GB/s",
-                        frac=pr["hbm"]["frac"], traffic=None, kernel="k_scan",
-                        peak_note="of measured (%s)" % pk["source"])
+        roof = dict(bound="alu", achieved=pr["alu"]["achieved"], peak=alu_peak, unit="TFLOP/s",
+                    frac=pr["alu"]["frac"], kernel="k_scan",
+                    traffic=(pr["dram"]["achieved"] * agg_ins["scan_ns"] / 1e9 / args.timing_steps * 1e9)
+                    if pr["dram"] else None,
+                    peak_note="derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz; "
+                              "3 flops per (q-x)^2 point" % pk["sm_max_mhz"],
+                    scan_byte_rate=pr["scan_byte_rate"], dram=pr["dram"])
         roof["kernel_share_of_step"] = agg_ins["scan_ns"] / 1e9 / t_ins
         for name, a in plain_runs:
             roof[name + "_k_scan"] = plain_roof(a)

@@ -293,7 +293,7 @@ typedef struct {
     uint32_t query_flags;  /* HK_Q_* applied to every batch (HK_Q_BF16 uses the
                               tensor-core form where the index has a copy)     */
     int32_t workers;       /* concurrent batches (threads, CUDA streams); 0 = 2,
-                              or 4 with persistent                            */
+                              or 3 with persistent                            */
     int32_t persistent;    /* 1: the tensor-core scans of all batches in flight
                               run in one resident launch that takes each
                               batch's scan from a device-resident ring while

@@ -333,19 +333,20 @@ void tc_wait_hooks(uint64_t &wait_ns, int &stall);
 
 // Served form of the tensor-core scan: one resident launch takes the scans
 // of many batches (jobs) from a ring as they are published.
-constexpr int kTcRing = 64;          // jobs in flight at most
+constexpr int kTcRing = 64;          // jobs in flight at most, per lane
+constexpr int kTcLanes = 2;          // lane 0 (approximate steps) is served before lane 1
 struct TcJob {                       // device memory, written before publication
     TcArgs args;
     int64_t total;                   // work items of the job (> 0)
     uint32_t seq;                    // publication number
     uint32_t pad;
 };
-struct TcServe {                     // the served launch's view of the ring
-    TcJob *jobs;                     // kTcRing
-    unsigned long long *word;        // (sequence of the current job << 32) | its next item
-    int32_t *done;                   // kTcRing items finished per slot
-    const volatile uint32_t *published;   // host-mapped: jobs published so far
-    volatile uint32_t *done_seq;     // host-mapped, kTcRing: last completed sequence per slot
+struct TcServe {                     // the served launch's view of the ring's lanes
+    TcJob *jobs;                     // kTcLanes * kTcRing (lane-major)
+    unsigned long long *word;        // per lane: (sequence of its current job << 32) | next item
+    int32_t *done;                   // kTcLanes * kTcRing items finished per slot
+    const volatile uint32_t *published;   // host-mapped, per lane: jobs published so far
+    volatile uint32_t *done_seq;     // host-mapped, kTcLanes * kTcRing: last completed sequence
     uint64_t idle_ns;                // a CTA leaves after this long without work
 };
 struct TcEngine;                     // host side (hk_tc.cu)
@@ -355,7 +356,7 @@ void tc_engine_destroy(TcEngine *e);
 // the served launch (starting it if none runs) and wait, bounded by
 // timeout_ns, until its items are done.  The caller's stream must have
 // produced the scan's inputs already (synchronised).
-void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout_ns);
+void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout_ns, int lane);
 struct TcEngineStats {
     long long launches;              // served launches started
     long long jobs;                  // jobs published

@@ -1407,7 +1407,9 @@ void tc_phase(hk_index *idx, Workspace &ws, const LeafView &v, const float *Qd, 
         int64_t items = 0;
         HK_CHECK_CUDA(cudaMemcpyAsync(&items, ws.item_off.p + v.L, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HK_CHECK_CUDA(cudaStreamSynchronize(s));
-        if (items > 0) tc_engine_run(ws.engine, t, items, 120ull * 1000000000ull);
+        // approximate steps (val 1) take the ring's first lane: they are
+        // short and every batch waits on one before its exact step
+        if (items > 0) tc_engine_run(ws.engine, t, items, 120ull * 1000000000ull, val == 1 ? 0 : 1);
     } else {
         if (tctimer) tctimer->mark(s);
         launch_tc_scan(t, s);

@@ -264,7 +264,7 @@ int hk_server_create(const hk_server_opts *opts, hk_server **out) {
             sv->opts.workers < 0)
             hk::fail(HK_EINVAL, "negative server option");
         if (sv->opts.persistent != 0 && sv->opts.persistent != 1) hk::fail(HK_EINVAL, "persistent must be 0 or 1");
-        const int nw = sv->opts.workers > 0 ? sv->opts.workers : (sv->opts.persistent ? 4 : 2);
+        const int nw = sv->opts.workers > 0 ? sv->opts.workers : (sv->opts.persistent ? 3 : 2);
         HK_CHECK_CUDA(cudaGetDevice(&sv->device));
         if (sv->opts.persistent) sv->engine = hk::tc_engine_create(kSideSMs);
         for (int i = 0; i < nw; ++i) {

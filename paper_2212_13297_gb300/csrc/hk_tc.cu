@@ -377,21 +377,27 @@ __device__ void describe_item(const TcArgs &A, int64_t it, TcItem &D, int lane) 
 }
 
 // Served form (one warp): claim the next item of the oldest published job
-// that has items left, copy that job's arguments into shared memory and
-// describe the item.  A claim is one compare-and-swap on the ring's word
-// (job sequence, next item), so an item is claimed once, and only while its
-// job is the current one (a ring slot is rewritten only after its job
-// completed).  Sets S.quit when no job came for V.idle_ns.
+// that has items left -- in lane 0 (approximate steps, short and on every
+// batch's critical path) before lane 1 -- copy that job's arguments into
+// shared memory and describe the item.  A claim is one compare-and-swap on
+// the lane's word (job sequence, next item), so an item is claimed once, and
+// only while its job is the lane's current one (a ring slot is rewritten only
+// after its job completed).  Sets S.quit when no job came for V.idle_ns.
 __device__ void serve_fetch(const TcServe &V, TcServeShared &S, int lane) {
     int slot = -1;
     long long item = 0;
     uint32_t seq = 0;
     if (lane == 0) {
         uint64_t idle0 = 0;
+        int ln = 0;
         for (;;) {
-            const unsigned long long w = atomicAdd(V.word, 0ull);
+            const unsigned long long w = atomicAdd(V.word + ln, 0ull);
             const uint32_t cur = (uint32_t)(w >> 32), i = (uint32_t)w;
-            if (cur == *V.published) {   // nothing published beyond the current job
+            if (cur == V.published[ln]) {   // nothing in this lane beyond its current job
+                if (ln + 1 < kTcLanes) {
+                    ++ln;
+                    continue;
+                }
                 const uint64_t now = global_ns();
                 if (idle0 == 0) {
                     idle0 = now;
@@ -399,19 +405,21 @@ __device__ void serve_fetch(const TcServe &V, TcServeShared &S, int lane) {
                     break;
                 }
                 __nanosleep(2000);
+                ln = 0;
                 continue;
             }
             idle0 = 0;
-            const int sl = (int)(cur % kTcRing);
+            const int sl = ln * kTcRing + (int)(cur % kTcRing);
             const long long total = __ldcg(&V.jobs[sl].total);
             const unsigned long long nw =
                 (long long)i < total ? w + 1 : ((unsigned long long)(cur + 1) << 32);
-            if (atomicCAS(V.word, w, nw) == w && (long long)i < total) {
+            if (atomicCAS(V.word + ln, w, nw) == w && (long long)i < total) {
                 slot = sl;
                 item = i;
                 seq = cur;
                 break;
             }
+            ln = 0;   // lost a race or finished a job: look at the first lane again
         }
     }
     slot = __shfl_sync(0xffffffffu, slot, 0);
@@ -1312,9 +1320,9 @@ struct TcEngine {
     DevBuf<TcJob> jobs;
     DevBuf<unsigned long long> word;
     DevBuf<int32_t> done;
-    uint32_t *ctl_h = nullptr;       // mapped: [0] published, [1 + slot] last completed sequence
+    uint32_t *ctl_h = nullptr;       // mapped: [lane] published, [kTcLanes + slot] last completed sequence
     uint32_t *ctl_d = nullptr;
-    uint32_t published = 0;
+    uint32_t published[kTcLanes] = {};
     bool launched = false;
     cudaEvent_t ev = nullptr;        // recorded after the last launch
     std::mutex mu;
@@ -1339,7 +1347,7 @@ void engine_launch(TcEngine *e) {
     V.word = e->word.p;
     V.done = e->done.p;
     V.published = e->ctl_d;
-    V.done_seq = e->ctl_d + 1;
+    V.done_seq = e->ctl_d + kTcLanes;
     V.idle_ns = e->idle_ns;
     k_tc_serve<<<e->ctas, kTcThreads, tc_serve_smem_bytes(), e->stream>>>(V);
     HK_CHECK_LAUNCH();
@@ -1369,14 +1377,15 @@ TcEngine *tc_engine_create(int spare_sms) {
     HK_CHECK_CUDA(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
     HK_CHECK_CUDA(cudaStreamCreateWithFlags(&e->pub, cudaStreamNonBlocking));
     HK_CHECK_CUDA(cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming));
-    e->jobs.alloc(kTcRing, e->pub);
-    e->word.alloc(1, e->pub);
-    e->done.alloc(kTcRing, e->pub);
-    HK_CHECK_CUDA(cudaMemsetAsync(e->word.p, 0, sizeof(unsigned long long), e->pub));
-    HK_CHECK_CUDA(cudaMemsetAsync(e->done.p, 0, kTcRing * sizeof(int32_t), e->pub));
-    HK_CHECK_CUDA(cudaHostAlloc((void **)&e->ctl_h, (1 + kTcRing) * sizeof(uint32_t), cudaHostAllocMapped));
-    e->ctl_h[0] = 0;
-    for (int i = 0; i < kTcRing; ++i) e->ctl_h[1 + i] = 0xffffffffu;
+    e->jobs.alloc(kTcLanes * kTcRing, e->pub);
+    e->word.alloc(kTcLanes, e->pub);
+    e->done.alloc(kTcLanes * kTcRing, e->pub);
+    HK_CHECK_CUDA(cudaMemsetAsync(e->word.p, 0, kTcLanes * sizeof(unsigned long long), e->pub));
+    HK_CHECK_CUDA(cudaMemsetAsync(e->done.p, 0, kTcLanes * kTcRing * sizeof(int32_t), e->pub));
+    HK_CHECK_CUDA(cudaHostAlloc((void **)&e->ctl_h, (kTcLanes + kTcLanes * kTcRing) * sizeof(uint32_t),
+                                cudaHostAllocMapped));
+    for (int i = 0; i < kTcLanes; ++i) e->ctl_h[i] = 0;
+    for (int i = 0; i < kTcLanes * kTcRing; ++i) e->ctl_h[kTcLanes + i] = 0xffffffffu;
     HK_CHECK_CUDA(cudaHostGetDevicePointer((void **)&e->ctl_d, e->ctl_h, 0));
     HK_CHECK_CUDA(cudaStreamSynchronize(e->pub));
     return e.release();
@@ -1399,20 +1408,20 @@ void tc_engine_stats(TcEngine *e, TcEngineStats *out) {
     *out = e->st;
 }
 
-void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout_ns) {
+void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout_ns, int lane) {
     using clock = std::chrono::steady_clock;
     const auto t0 = clock::now();
     auto late = [&] {
         return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - t0).count() >
                timeout_ns;
     };
-    volatile uint32_t *done_seq = e->ctl_h + 1;
+    volatile uint32_t *done_seq = e->ctl_h + kTcLanes;
     uint32_t seq;
     int slot;
     {
         std::unique_lock<std::mutex> lk(e->mu);
-        seq = e->published;
-        slot = (int)(seq % kTcRing);
+        seq = e->published[lane];
+        slot = lane * kTcRing + (int)(seq % kTcRing);
         // the slot's previous job must have completed before it is rewritten
         while (seq >= (uint32_t)kTcRing && done_seq[slot] != seq - kTcRing) {
             if (late()) fail(HK_ETIMEOUT, "served scan: ring slot %d still busy", slot);
@@ -1431,8 +1440,8 @@ void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout
         HK_CHECK_CUDA(cudaMemsetAsync(e->done.p + slot, 0, sizeof(int32_t), e->pub));
         HK_CHECK_CUDA(cudaStreamSynchronize(e->pub));
         std::atomic_thread_fence(std::memory_order_seq_cst);
-        e->published = seq + 1;
-        *(volatile uint32_t *)e->ctl_h = seq + 1;
+        e->published[lane] = seq + 1;
+        *(volatile uint32_t *)(e->ctl_h + lane) = seq + 1;
         e->st.jobs += 1;
         if (engine_running(e)) {
             e->st.jobs_inflight += 1;
@@ -1441,7 +1450,7 @@ void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout
         }
         engine_note_coll(e, a.Xb);
     }
-    for (;;) {
+    for (int spin = 0;; ++spin) {
         if (done_seq[slot] == seq) break;
         if (late()) fail(HK_ETIMEOUT, "served scan: job %u not finished in time", seq);
         if (!engine_running(e)) {
@@ -1456,7 +1465,11 @@ void tc_engine_run(TcEngine *e, const TcArgs &a, int64_t items, uint64_t timeout
                 engine_launch(e);   // it went idle before this job was published
             }
         }
-        std::this_thread::sleep_for(std::chrono::microseconds(10));
+        // spin (yielding) through short jobs, then sleep between looks
+        if (spin < 4096)
+            std::this_thread::yield();
+        else
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     std::atomic_thread_fence(std::memory_order_seq_cst);
 }
