@@ -58,15 +58,30 @@ WORKLOADS = {
 # shape; a full launch's traffic is that multiple of its own algorithmic bytes.
 # Each entry holds the SHA-256 prefix of the kernel source it was taken on;
 # once the source differs, traffic is reported as null until re-captured.
-TRAFFIC_RATIO = {}   # (kernel, form): dict(exact=r, approx=r, src=sha16, capture=description)
-KERNEL_SOURCE = {"k_tc_scan": "paper_2212_13297_gb300/csrc/hk_tc.cu",
-                 "k_scan": "paper_2212_13297_gb300/csrc/hk_query.cu"}
+TRAFFIC_RATIO = {   # (kernel, form): dict(exact=r, approx=r, src=sha16, capture=description)
+    ("k_tc_scan", "fp16"): dict(
+        exact=3.2185e9 / 2.08e9, approx=None, src="e37686c97a7903c2",
+        capture="the exact-step launch of bench.py --workload tcleaf100k2k (4M random walks x 256, leaf 100K, "
+                "2000 hard queries: 3.2185 GB of DRAM, L2 hit 74.3%, against 2.08 GB of 16-bit rows and norms)"),
+}
+# each kernel's source file and the first line of its definition; the hash
+# covers the definition's text, up to the closing brace at the start of a line
+KERNEL_SOURCE = {
+    "k_tc_scan": ("paper_2212_13297_gb300/csrc/hk_tc.cu",
+                  "__global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {"),
+    "k_scan": ("paper_2212_13297_gb300/csrc/hk_query.cu",
+               "__global__ void __launch_bounds__(kBT, 4) k_scan(ScanArgs A) {"),
+}
 
 
 def source_sha(kernel):
+    """SHA-256 prefix of the kernel definition's source text."""
     import hashlib
-    with open(os.path.join(ROOT, KERNEL_SOURCE[kernel]), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    path, head = KERNEL_SOURCE[kernel]
+    text = open(os.path.join(ROOT, path)).read()
+    a = text.index(head)
+    b = text.index("\n}\n", a)
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
 def traffic_ratio(kernel, form):
@@ -857,7 +872,8 @@ def main():
             roof["approx_step_launches"] = dict(
                 kernel="k_tc_scan", share_of_step=tca_s / t_ins,
                 bulk_copy_rate=dict(achieved=a["tc_approx_bytes"] / tca_s / 1e9, unit="GB/s"),
-                traffic=tr["approx"] * a.get("tc_approx_bytes", 0) / args.timing_steps if tr else None,
+                traffic=tr["approx"] * a.get("tc_approx_bytes", 0) / args.timing_steps
+                if tr and tr["approx"] else None,
                 note="the same kernel on each query's approximate-search leaves (few queries per "
                      "leaf: bound by the 16-bit rows it streams, not by the MMA)")
         for name, a in plain_runs:

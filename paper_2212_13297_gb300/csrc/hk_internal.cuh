@@ -140,7 +140,8 @@ struct Workspace {
     DevBuf<float> cand_lb;      // nq * cand_C  lower bound D~ - E
     DevBuf<uint32_t> Uinit;     // retry pass: starting bounds
     DevBuf<int32_t> sel;        // retry pass: rows of the batch it answers
-    DevBuf<uint8_t> tree_alive; // HK_Q_TREE: T * nq, node-major: node stays for the query
+    DevBuf<unsigned long long> tree_front;  // HK_Q_TREE: two frontiers of (node << 32 | query)
+    DevBuf<int32_t> tree_cnt;   // HK_Q_TREE: frontier sizes, one per level
     struct TcEngine *engine = nullptr;   // served: tensor-core scans go to this resident launch
     // graph mode: the captured pass (reading Q, writing out_*) and its key
     cudaGraphExec_t gexec = nullptr;

@@ -295,39 +295,76 @@ __global__ void __launch_bounds__(128) k_tree_approx(const double *__restrict__ 
 
 // a4 with HK_Q_TREE: candidate leaves by a top-down pass over the tree
 // (FindCandidateLeaves over the hierarchy of node synopses, Sec. 3.3-3.4).
-// At one level, a node's LB_EAPCA is evaluated for a query only if the
-// node's parent stayed for it (the root always), and the node stays unless
-// its certified LB exceeds U: every series below a node is at least its LB
-// away, so a pruned node prunes its whole subtree.  A leaf that stays
-// becomes a candidate unless the approximate search visited it.
-// alive[node * nq + q], node-major.
-__global__ void k_tree_level(const double *__restrict__ qseg, int64_t S, TreeView tv,
-                             const int32_t *__restrict__ nodes, int cnt, int nq, const uint32_t *__restrict__ U,
-                             uint8_t *__restrict__ alive, uint8_t *__restrict__ mask, int32_t *__restrict__ qcand,
-                             double *__restrict__ lb, long long *__restrict__ stats) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// A frontier holds the (internal node, query) pairs that stayed at one
+// level; each pass evaluates LB_EAPCA for the two children of every pair in
+// it and keeps a child unless its certified LB exceeds U: every series below
+// a node is at least the node's LB away, so a pruned node prunes its whole
+// subtree, and the work follows the pairs that stay.  A leaf that stays
+// becomes a candidate unless the approximate search visited it; an internal
+// node goes to the next frontier.  A pair is packed as (node << 32) | query.
+__global__ void k_tree_expand(const double *__restrict__ qseg, int64_t S, TreeView tv,
+                              const unsigned long long *__restrict__ in, const int32_t *__restrict__ n_in,
+                              unsigned long long *__restrict__ out, int32_t *__restrict__ n_out, int nq,
+                              const uint32_t *__restrict__ U, uint8_t *__restrict__ mask,
+                              int32_t *__restrict__ qcand, double *__restrict__ lb, long long *__restrict__ stats) {
+    const int cnt = *n_in;
+    const int lane = threadIdx.x & 31;
     long long ev = 0;
-    if (t < (int64_t)cnt * nq) {
-        const int64_t u = nodes[t / nq];
-        const int q = (int)(t % nq);
-        const int32_t p = tv.parent[u];
-        uint8_t a = 0;
-        if (p < 0 || alive[(int64_t)p * nq + q]) {
-            const double v = node_lb(tv, qseg, S, q, u);
-            ev = 1;
-            a = !(lb_lower(v) > (double)__uint_as_float(U[q]));
-            if (u < tv.L) {
-                lb[(int64_t)q * tv.L + u] = v;
-                if (a && mask[u * nq + q] == 0) {
-                    mask[u * nq + q] = 2;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < 2 * (int64_t)cnt;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        bool push = false;
+        unsigned long long pair = 0;
+        if (i < 2 * (int64_t)cnt) {
+            const unsigned long long p = in[i >> 1];
+            const int64_t u = (int64_t)(p >> 32);
+            const int q = (int)(p & 0xffffffffu);
+            const int64_t c = (i & 1) ? tv.right[u] : tv.left[u];
+            const double v = node_lb(tv, qseg, S, q, c);
+            ++ev;
+            const bool stays = !(lb_lower(v) > (double)__uint_as_float(U[q]));
+            if (c < tv.L) {
+                lb[(int64_t)q * tv.L + c] = v;
+                if (stays && mask[c * nq + q] == 0) {
+                    mask[c * nq + q] = 2;
                     atomicAdd(&qcand[q], 1);
                 }
+            } else if (stays) {
+                push = true;
+                pair = ((unsigned long long)c << 32) | (unsigned)q;
             }
         }
-        alive[u * nq + q] = a;
+        // warp-aggregated append to the next frontier
+        const unsigned bal = __ballot_sync(0xffffffffu, push);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(n_out, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (push) out[base + __popc(bal & ((1u << lane) - 1))] = pair;
     }
     ev = warp_sum_ll(ev);
-    if ((threadIdx.x & 31) == 0 && ev) stat_add(&stats[ST_LB_EVALS], ev);
+    if (lane == 0 && ev) stat_add(&stats[ST_LB_EVALS], ev);
+}
+
+// The first frontier: the root for every query whose root LB stays (one
+// evaluation per query); a single-leaf tree makes its leaf a candidate.
+__global__ void k_tree_root(const double *__restrict__ qseg, int64_t S, TreeView tv, int64_t root, int nq,
+                            const uint32_t *__restrict__ U, unsigned long long *__restrict__ out,
+                            int32_t *__restrict__ n_out, uint8_t *__restrict__ mask, int32_t *__restrict__ qcand,
+                            double *__restrict__ lb, long long *__restrict__ stats) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double v = node_lb(tv, qseg, S, q, root);
+    stat_add(&stats[ST_LB_EVALS], 1);
+    const bool stays = !(lb_lower(v) > (double)__uint_as_float(U[q]));
+    if (root < tv.L) {
+        lb[(int64_t)q * tv.L + root] = v;
+        if (stays && mask[root * nq + q] == 0) {
+            mask[root * nq + q] = 2;
+            atomicAdd(&qcand[q], 1);
+        }
+    } else if (stays) {
+        out[atomicAdd(n_out, 1)] = ((unsigned long long)root << 32) | (unsigned)q;
+    }
 }
 
 // a3 (selection): the leaves the approximate search visits: ascending
@@ -1732,14 +1769,25 @@ void query_pass(hk_index *idx, Workspace &ws, const float *Qd, int nq, int k, co
     {
         const int64_t pairs = L * (int64_t)nq;
         if (tree) {
-            ws.tree_alive.reserve((size_t)idx->T * nq, s);
+            // frontiers of (internal node, query) pairs, one pass per level;
+            // a level holds fewer internal nodes than the tree has leaves
+            const size_t cap = (size_t)nq * (size_t)std::max<int64_t>(1, L);
             const int levels = (int)idx->h_level_off.size() - 1;
-            for (int d = 0; d < levels; ++d) {
-                const int cnt = idx->h_level_off[d + 1] - idx->h_level_off[d];
-                const int64_t work = (int64_t)cnt * nq;
-                k_tree_level<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(
-                    ws.qseg.p, idx->S, tv, idx->level_nodes.p + idx->h_level_off[d], cnt, nq, ws.U.p,
-                    ws.tree_alive.p, ws.mask.p, ws.qcand.p, ws.lb.p, (long long *)ws.stats.p);
+            ws.tree_front.reserve(2 * cap, s);
+            ws.tree_cnt.reserve((size_t)levels + 1, s);
+            HK_CHECK_CUDA(cudaMemsetAsync(ws.tree_cnt.p, 0, ((size_t)levels + 1) * sizeof(int32_t), s));
+            const int64_t root = L > 1 ? L : 0;
+            k_tree_root<<<(nq + 255) / 256, 256, 0, s>>>(ws.qseg.p, idx->S, tv, root, nq, ws.U.p,
+                                                         ws.tree_front.p, ws.tree_cnt.p, ws.mask.p, ws.qcand.p,
+                                                         ws.lb.p, (long long *)ws.stats.p);
+            HK_CHECK_LAUNCH();
+            const int grid = sm_count() * 8;
+            for (int d = 0; d + 1 < levels; ++d) {
+                unsigned long long *fin = ws.tree_front.p + (d & 1) * cap;
+                unsigned long long *fout = ws.tree_front.p + ((d + 1) & 1) * cap;
+                k_tree_expand<<<grid, 256, 0, s>>>(ws.qseg.p, idx->S, tv, fin, ws.tree_cnt.p + d, fout,
+                                                   ws.tree_cnt.p + d + 1, nq, ws.U.p, ws.mask.p, ws.qcand.p,
+                                                   ws.lb.p, (long long *)ws.stats.p);
                 HK_CHECK_LAUNCH();
             }
         } else {
