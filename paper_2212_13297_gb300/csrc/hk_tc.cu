@@ -222,18 +222,26 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                      smem_u32(bar))
                  : "memory");
 }
-// Issue one 32-column TMEM load (lanes of this warp's quarter); the values
-// are valid only after tmem_wait_ld().
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+// Issue one 64-column TMEM load (lanes of this warp's quarter; columns in
+// register order, 32 per row of r); the values are valid only after
+// tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld64_issue(uint32_t taddr, uint32_t (&r)[2][32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+          "=r"(r[0][7]), "=r"(r[0][8]), "=r"(r[0][9]), "=r"(r[0][10]), "=r"(r[0][11]), "=r"(r[0][12]), "=r"(r[0][13]),
+          "=r"(r[0][14]), "=r"(r[0][15]), "=r"(r[0][16]), "=r"(r[0][17]), "=r"(r[0][18]), "=r"(r[0][19]),
+          "=r"(r[0][20]), "=r"(r[0][21]), "=r"(r[0][22]), "=r"(r[0][23]), "=r"(r[0][24]), "=r"(r[0][25]),
+          "=r"(r[0][26]), "=r"(r[0][27]), "=r"(r[0][28]), "=r"(r[0][29]), "=r"(r[0][30]), "=r"(r[0][31]),
+          "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]), "=r"(r[1][6]),
+          "=r"(r[1][7]), "=r"(r[1][8]), "=r"(r[1][9]), "=r"(r[1][10]), "=r"(r[1][11]), "=r"(r[1][12]), "=r"(r[1][13]),
+          "=r"(r[1][14]), "=r"(r[1][15]), "=r"(r[1][16]), "=r"(r[1][17]), "=r"(r[1][18]), "=r"(r[1][19]),
+          "=r"(r[1][20]), "=r"(r[1][21]), "=r"(r[1][22]), "=r"(r[1][23]), "=r"(r[1][24]), "=r"(r[1][25]),
+          "=r"(r[1][26]), "=r"(r[1][27]), "=r"(r[1][28]), "=r"(r[1][29]), "=r"(r[1][30]), "=r"(r[1][31])
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
@@ -625,11 +633,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_scan(TcArgs A) {
                 const float thr = U - q2e;   // lo <= U  <=>  x2e - qa|x| - 2v <= U - q2e
                 const float2 *xs = sX + (gt % kNormSlots) * kTcN;
                 uint32_t raw[kEpiChunks][32];
-#pragma unroll
-                for (int h = 0; h < kEpiChunks; ++h)
-                    tmem_ld32_issue(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                                        (uint32_t)(b * kTcN + (cq * kEpiChunks + h) * 32),
-                                    raw[h]);
+                static_assert(kEpiChunks == 2, "one 64-column load per thread and tile");
+                tmem_ld64_issue(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * kTcN + cq * 64), raw);
                 tmem_wait_ld();
                 // the accumulator is in registers: release it to the MMAs
                 // before filtering
@@ -939,11 +944,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_serve(TcServe V) {
                 const float thr = U - q2e;   // lo <= U  <=>  x2e - qa|x| - 2v <= U - q2e
                 const float2 *xs = sX + (gt % kNormSlots) * kTcN;
                 uint32_t raw[kEpiChunks][32];
-#pragma unroll
-                for (int h = 0; h < kEpiChunks; ++h)
-                    tmem_ld32_issue(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                                        (uint32_t)(b * kTcN + (cq * kEpiChunks + h) * 32),
-                                    raw[h]);
+                static_assert(kEpiChunks == 2, "one 64-column load per thread and tile");
+                tmem_ld64_issue(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * kTcN + cq * 64), raw);
                 tmem_wait_ld();
                 // the accumulator is in registers: release it to the MMAs
                 // before filtering
