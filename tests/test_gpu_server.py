@@ -193,3 +193,32 @@ def test_budget_admits_as_memory_frees(hb, two_collections):
     assert st["errors"] == 0 and st["served"] == 150
     assert 0 < st["budget_peak"] <= budget
     assert st["max_batch"] < 150
+
+
+def test_persistent_scan_relaunches_after_idle(hb, oracle_lib, two_collections):
+    """The resident launch leaves after a short idle period; a batch that
+    arrives later starts another launch.  A collection without a 16-bit copy
+    (float32 path) is served beside it."""
+    import time
+    c = two_collections
+    sv = hb.Server(max_batch=16, query_flags=hb.HK_Q_BF16, workers=2, persistent=1)
+    coll16 = sv.add(c["idx"][1])                 # float16 copy: tensor-core scans
+    coll32 = sv.add(c["idx"][0])                 # no 16-bit copy: float32 path
+    got = []
+    for wave in range(3):
+        ts = [(sv.submit(coll16, c["Q"][1][wave * 10 + i], 7), 1, wave * 10 + i) for i in range(10)]
+        ts += [(sv.submit(coll32, c["Q"][0][wave * 10 + i], 4), 0, wave * 10 + i) for i in range(5)]
+        for t, ci, qi in ts:
+            k = 7 if ci == 1 else 4
+            r = sv.poll(t, k, timeout_us=60_000_000)
+            assert r is not None
+            got.append((ci, qi, k, r))
+        time.sleep(0.05)                         # far longer than the launch's idle period
+    st = sv.stats()
+    sv.close()
+    assert st["errors"] == 0 and st["scan_launches"] >= 3
+    for ci, qi, k, r in got:
+        flags = hb.HK_Q_BF16 if ci == 1 else 0
+        ids, dist, _ = c["idx"][ci].query(c["Q"][ci][qi:qi + 1], k, flags=flags)
+        np.testing.assert_array_equal(r[0], ids[0])
+        np.testing.assert_array_equal(r[1], dist[0])
