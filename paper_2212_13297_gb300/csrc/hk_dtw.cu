@@ -206,8 +206,91 @@ struct DtwScanArgs {
     long long *st;
 };
 
-// a5-a6: one (leaf, query) pair per block at a time (persistent grid), one
-// series per thread: word bound, LB_Keogh, then DTW with early abandoning.
+// Float32 DTW of series x against the query in shared memory, rows kept in
+// registers (cell w of row i is column j = i + w - r; cells past 2r stay
+// +inf), abandoned as soon as a row's smallest cell exceeds T: returns the
+// distance, and sets `abandoned` if it stopped early.  Rows whose band lies inside [0, n) take
+// a path without the column checks; the arithmetic per cell is the same.
+template <int KW>
+__device__ __forceinline__ float dtw_band(const float *__restrict__ x, const float *__restrict__ qs, int n,
+                                          int r, float T, long long &cells, bool &abandoned) {
+    float prev[KW + 1], cur[KW], xw[KW + 1];
+    const int wmax = 2 * r;
+#pragma unroll
+    for (int w = 0; w < KW; ++w) {
+        prev[w] = INFINITY;
+        cur[w] = INFINITY;
+        const int j = w - r;                     // the window of row 0
+        xw[w] = (w <= wmax && j >= 0 && j < n) ? x[j] : 0.0f;
+    }
+    prev[KW] = INFINITY;
+    xw[KW] = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        const float qi = qs[i];
+        float rowmin = INFINITY;
+        if (i >= r && i + r < n && i > 0) {
+            // every cell of the row inside the matrix
+#pragma unroll
+            for (int w = 0; w < KW; ++w) {
+                if (w <= wmax) {
+                    const float c = w >= 1 ? cur[w - 1] : INFINITY;
+                    const float best = fminf(fminf(prev[w], prev[w + 1]), c);
+                    const float d = __fsub_rn(qi, xw[w]);
+                    const float v = __fadd_rn(__fmul_rn(d, d), best);
+                    cur[w] = v;
+                    rowmin = fminf(rowmin, v);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < KW; ++w) {
+                if (w <= wmax) {
+                    const int j = i + w - r;
+                    float v = INFINITY;
+                    if (j >= 0 && j < n) {
+                        float best;
+                        if (i == 0 && j == 0) {
+                            best = 0.0f;
+                        } else {
+                            const float c = w >= 1 ? cur[w - 1] : INFINITY;
+                            best = fminf(fminf(prev[w], prev[w + 1]), c);
+                        }
+                        const float d = __fsub_rn(qi, xw[w]);
+                        v = __fadd_rn(__fmul_rn(d, d), best);
+                    }
+                    cur[w] = v;
+                    rowmin = fminf(rowmin, v);
+                }
+            }
+        }
+        cells += wmax + 1;
+        if (rowmin > T) {
+            abandoned = true;
+            return INFINITY;
+        }
+        const int jn = i + 1 + r;              // the column entering the band
+        const float xn = jn < n ? x[jn] : 0.0f;
+#pragma unroll
+        for (int w = 0; w < KW; ++w) {
+            prev[w] = cur[w];
+            xw[w] = (w == wmax) ? xn : xw[w + 1];
+        }
+    }
+    float d = INFINITY;                        // column n - 1 of row n - 1: cell r
+#pragma unroll
+    for (int w = 0; w < KW; ++w)
+        if (w == r) d = prev[w];
+    return d;
+}
+
+constexpr int kDtwWindow = 1024;   // series a block screens before their DTWs
+
+// a5-a6: one (leaf, query) pair per block at a time (persistent grid).  The
+// block screens a window of the leaf's series (word bound, then LB_Keogh:
+// one series per thread), queues the survivors in shared memory, then its
+// threads take queued series one at a time for the DTW with early
+// abandoning, so a thread whose series ended early takes the next.
+template <int KW>
 __global__ void __launch_bounds__(kDtwThreads) k_dtw_scan(DtwScanArgs A) {
     extern __shared__ float sh[];
     const int n = A.n, r = A.r;
@@ -215,6 +298,8 @@ __global__ void __launch_bounds__(kDtwThreads) k_dtw_scan(DtwScanArgs A) {
     __shared__ float B[kAlpha + 1];
     __shared__ float pl[kWord], pu[kWord];
     __shared__ int64_t s_e;
+    __shared__ int s_qn, s_take;
+    __shared__ int16_t s_queue[kDtwWindow];
     for (int j = threadIdx.x; j <= kAlpha; j += blockDim.x)
         B[j] = j == 0 ? -INFINITY : (j == kAlpha ? INFINITY : A.bp[j - 1]);
     const float w_sax = (float)(n / kWord);
@@ -242,100 +327,65 @@ __global__ void __launch_bounds__(kDtwThreads) k_dtw_scan(DtwScanArgs A) {
         const float u = __uint_as_float(A.U[q]);
         const float T = __fmul_ru(u, 1.0f + A.rho);
         const int64_t s0 = A.leaf_off[leaf], s1 = A.leaf_off[leaf + 1];
-        for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-            ++c_cand;
-            if (A.use_sax) {
-                const uint4 w4 = *reinterpret_cast<const uint4 *>(A.sax + s * kWord);
-                const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
-                float acc = 0.0f;
+        for (int64_t w0 = s0; w0 < s1; w0 += kDtwWindow) {
+            const int64_t w1 = min(w0 + (int64_t)kDtwWindow, s1);
+            if (threadIdx.x == 0) {
+                s_qn = 0;
+                s_take = 0;
+            }
+            __syncthreads();
+            for (int64_t s = w0 + threadIdx.x; s < w1; s += blockDim.x) {
+                ++c_cand;
+                if (A.use_sax) {
+                    const uint4 w4 = *reinterpret_cast<const uint4 *>(A.sax + s * kWord);
+                    const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                    float acc = 0.0f;
 #pragma unroll
-                for (int i = 0; i < kWord; ++i) {
-                    const int sym = (wv[i >> 2] >> ((i & 3) * 8)) & 0xff;
-                    const float a = __fsub_rd(B[sym], pu[i]);        // cell low end - PAA(U)
-                    const float b = __fsub_rd(pl[i], B[sym + 1]);    // PAA(L) - cell high end
-                    const float g = fmaxf(fmaxf(a, b), 0.0f);
-                    acc = __fmaf_rd(g, g, acc);
+                    for (int i = 0; i < kWord; ++i) {
+                        const int sym = (wv[i >> 2] >> ((i & 3) * 8)) & 0xff;
+                        const float a = __fsub_rd(B[sym], pu[i]);        // cell low end - PAA(U)
+                        const float b = __fsub_rd(pl[i], B[sym + 1]);    // PAA(L) - cell high end
+                        const float g = fmaxf(fmaxf(a, b), 0.0f);
+                        acc = __fmaf_rd(g, g, acc);
+                    }
+                    if (__fmul_rd(acc, w_sax) > u) {
+                        ++c_sax;
+                        continue;
+                    }
                 }
-                if (__fmul_rd(acc, w_sax) > u) {
-                    ++c_sax;
+                const float *x = A.X + s * n;
+                // LB_Keogh from the raw points, rounded down, stopping once above U
+                float lbk = 0.0f;
+                bool pruned = false;
+                for (int j0 = 0; j0 < n && !pruned; j0 += 16) {
+#pragma unroll
+                    for (int j = j0; j < j0 + 16; ++j) {
+                        const float xv = x[j];
+                        const float g = fmaxf(fmaxf(__fsub_rd(Ls[j], xv), __fsub_rd(xv, Us[j])), 0.0f);
+                        lbk = __fmaf_rd(g, g, lbk);
+                    }
+                    pruned = lbk > u;
+                }
+                if (pruned) {
+                    ++c_keogh;
                     continue;
                 }
+                s_queue[atomicAdd(&s_qn, 1)] = (int16_t)(s - w0);
             }
-            const float *x = A.X + s * n;
-            // LB_Keogh from the raw points, rounded down, stopping once above U
-            float lbk = 0.0f;
-            bool pruned = false;
-            for (int j0 = 0; j0 < n && !pruned; j0 += 16) {
-#pragma unroll
-                for (int j = j0; j < j0 + 16; ++j) {
-                    const float xv = x[j];
-                    const float g = fmaxf(fmaxf(__fsub_rd(Ls[j], xv), __fsub_rd(xv, Us[j])), 0.0f);
-                    lbk = __fmaf_rd(g, g, lbk);
+            __syncthreads();
+            const int qn = s_qn;
+            for (;;) {
+                const int idx = atomicAdd(&s_take, 1);
+                if (idx >= qn) break;
+                const int64_t s = w0 + s_queue[idx];
+                bool abandoned = false;
+                const float d = dtw_band<KW>(A.X + s * n, qs, n, r, T, c_cells, abandoned);
+                if (abandoned) {
+                    ++c_ab;
+                    continue;
                 }
-                pruned = lbk > u;
-            }
-            if (pruned) {
-                ++c_keogh;
-                continue;
-            }
-            // DTW in float32 over the band, rows kept in registers: cell w of
-            // a row is column j = i + w - r
-            float prev[kW], cur[kW], xw[kW];
-#pragma unroll
-            for (int w = 0; w < kW; ++w) {
-                prev[w] = INFINITY;
-                cur[w] = INFINITY;
-                const int j = w - r;                     // the window of row 0
-                xw[w] = (w <= 2 * r && j >= 0 && j < n) ? x[j] : 0.0f;
-            }
-            bool abandoned = false;
-            for (int i = 0; i < n; ++i) {
-                const float qi = qs[i];
-                float rowmin = INFINITY;
-#pragma unroll
-                for (int w = 0; w < kW; ++w) {
-                    if (w > 2 * r) break;
-                    const int j = i + w - r;
-                    float v = INFINITY;
-                    if (j >= 0 && j < n) {
-                        float best;
-                        if (i == 0 && j == 0) {
-                            best = 0.0f;
-                        } else {
-                            const float a = prev[w];
-                            const float b = (w + 1 <= 2 * r) ? prev[w + 1] : INFINITY;
-                            const float c = (w >= 1) ? cur[w - 1] : INFINITY;
-                            best = fminf(fminf(a, b), c);
-                        }
-                        const float d = __fsub_rn(qi, xw[w]);
-                        v = __fadd_rn(__fmul_rn(d, d), best);
-                    }
-                    cur[w] = v;
-                    rowmin = fminf(rowmin, v);
-                }
-                c_cells += 2 * r + 1;
-                if (rowmin > T) {
-                    abandoned = true;
-                    break;
-                }
-                const int jn = i + 1 + r;              // the column entering the band
-                const float xn = jn < n ? x[jn] : 0.0f;
-#pragma unroll
-                for (int w = 0; w < kW; ++w) {
-                    prev[w] = cur[w];
-                    xw[w] = (w == 2 * r) ? xn : (w < kW - 1 ? xw[w + 1] : 0.0f);
-                }
-            }
-            if (abandoned) {
-                ++c_ab;
-                continue;
-            }
-            ++c_full;
-            float d = INFINITY;                        // column n - 1 of row n - 1: cell r
-#pragma unroll
-            for (int w = 0; w < kW; ++w)
-                if (w == r) d = prev[w];
-            if (d <= T) {
+                ++c_full;
+                if (!(d <= T)) continue;
                 const int slot = atomicAdd(&A.pool_cnt[q], 1);
                 if (slot < A.pool_C) {
                     A.pool_d[(int64_t)q * A.pool_C + slot] = d;
@@ -344,6 +394,7 @@ __global__ void __launch_bounds__(kDtwThreads) k_dtw_scan(DtwScanArgs A) {
                     atomicOr(&A.qflag[q], 1);
                 }
             }
+            __syncthreads();
         }
     }
     c_cand = warp_sum_ll(c_cand);
@@ -663,7 +714,15 @@ void run_query_dtw(hk_index *idx, const float *Qd, int nq, int k, int band, cons
         a.pool_C = C;
         a.qflag = w.qflag.p;
         a.st = w.stats.p;
-        k_dtw_scan<<<sms * 8, kDtwThreads, smem, s>>>(a);
+        // band cells rounded up to a compiled width
+        if (r <= 4)
+            k_dtw_scan<9><<<sms * 8, kDtwThreads, smem, s>>>(a);
+        else if (r <= 8)
+            k_dtw_scan<17><<<sms * 8, kDtwThreads, smem, s>>>(a);
+        else if (r <= 12)
+            k_dtw_scan<25><<<sms * 8, kDtwThreads, smem, s>>>(a);
+        else
+            k_dtw_scan<kW><<<sms * 8, kDtwThreads, smem, s>>>(a);
         HK_CHECK_LAUNCH();
         k_dtw_kth<<<nq, 256, 0, s>>>(w.pool_d.p, w.pool_cnt.p, C, k, rho, w.U.p);
         HK_CHECK_LAUNCH();
