@@ -332,6 +332,16 @@ typedef struct {
  */
 int hk_server_create(const hk_server_opts *opts, hk_server **out);
 int hk_server_add(hk_server *sv, hk_index *idx, int32_t *coll_id);
+/*
+ * hk_server_add_opts -- hk_server_add with the query configuration this
+ * collection's batches use, e.g. the opts hk_tune chose for it (the paper
+ * tunes its parameters per workload, Sec. 4.2): l_max, EAPCA_TH, SAX_TH,
+ * query_group, series_tile and flags, checked as hk_query checks them
+ * (HK_EINVAL otherwise).  HK_Q_TIMING and HK_Q_GRAPH are dropped.  The
+ * server's query_flags do not apply to this collection.  opts NULL: as
+ * hk_server_add.  Answers equal hk_query's with the same opts.
+ */
+int hk_server_add_opts(hk_server *sv, hk_index *idx, const hk_query_opts *opts, int32_t *coll_id);
 /* q: host pointer to n floats (copied before return); k <= min(N, 1024). */
 int hk_submit(hk_server *sv, int32_t coll_id, const float *q, int32_t k,
               uint64_t *ticket);

@@ -97,7 +97,7 @@ EXPORTS = ["hk_build", "hk_free", "hk_index_info_get", "hk_query", "hk_query_dtw
            "hk_scan_knn_noalloc",
            "hk_isax_breakpoints", "hk_index_export", "hk_index_export_tree", "hk_debug_lb_eapca",
            "hk_debug_lb_sax",
-           "hk_debug_tc_dist", "hk_server_create", "hk_server_add", "hk_submit", "hk_poll",
+           "hk_debug_tc_dist", "hk_server_create", "hk_server_add", "hk_server_add_opts", "hk_submit", "hk_poll",
            "hk_server_stats_get", "hk_server_destroy", "hk_tune", "hk_save", "hk_load",
            "hk_query_opts_default", "hk_debug_device_allocs", "hk_debug_fail_device_alloc",
            "hk_debug_tc_wait", "hk_last_error", "hk_version"]
@@ -134,6 +134,7 @@ def lib():
         L.hk_debug_tc_dist.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
         L.hk_server_create.argtypes = [ctypes.POINTER(hk_server_opts), ctypes.POINTER(vp)]
         L.hk_server_add.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+        L.hk_server_add_opts.argtypes = [vp, vp, ctypes.POINTER(hk_query_opts), ctypes.POINTER(ctypes.c_int32)]
         L.hk_submit.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int32,
                                 ctypes.POINTER(ctypes.c_uint64)]
         L.hk_poll.argtypes = [vp, ctypes.c_uint64, vp, vp, ctypes.c_int32,
@@ -375,7 +376,18 @@ class Server:
         self._h = h
         self._n = {}
 
-    def add(self, index):
+    def add(self, index, opts=None):
+        """Register an index; opts (hk_query keyword arguments, e.g. the
+        dict Index.tune returns) become that collection's query configuration
+        (hk_server_add_opts)."""
+        if opts is not None:
+            o = hk_query_opts(int(opts.get("l_max", 0)), float(opts.get("eapca_th", -1.0)),
+                              float(opts.get("sax_th", -1.0)), int(opts.get("flags", 0)),
+                              int(opts.get("query_group", 0)), int(opts.get("series_tile", 0)))
+            c = ctypes.c_int32()
+            _check(lib().hk_server_add_opts(self._h, index._h, ctypes.byref(o), ctypes.byref(c)))
+            self._n[c.value] = index.n
+            return c.value
         c = ctypes.c_int32()
         _check(lib().hk_server_add(self._h, index._h, ctypes.byref(c)))
         self._n[c.value] = index.n

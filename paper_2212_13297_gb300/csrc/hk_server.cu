@@ -78,6 +78,8 @@ struct hk_server {
     int64_t budget_used = 0;          // device bytes the batches in flight hold
     std::condition_variable cv_mem;   // budget freed
     std::vector<hk_index *> colls;
+    std::vector<hk_query_opts> copts;  // per collection: its query configuration
+    std::vector<char> has_copts;       // 1: copts applies, 0: the server's query_flags
     std::mutex mu;
     std::condition_variable cv_work;   // requests arrived / shutdown
     std::condition_variable cv_done;   // a request completed
@@ -144,6 +146,8 @@ void worker_loop(hk_server *sv, Worker *w) {
         std::vector<std::shared_ptr<Request>> batch;
         int coll = -1;
         int64_t reserved = 0;
+        hk_query_opts copt{};
+        bool has_copt = false;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             for (;;) {
@@ -182,6 +186,8 @@ void worker_loop(hk_server *sv, Worker *w) {
                 batch.push_back(sv->queues[coll].front());
                 sv->queues[coll].pop_front();
             }
+            has_copt = sv->has_copts[coll] != 0;
+            if (has_copt) copt = sv->copts[coll];
             if (sv->opts.hbm_budget > 0) {
                 reserved = batch_bytes(sv->colls[coll], kmax, (int)batch.size());
                 sv->budget_used += reserved;
@@ -207,9 +213,11 @@ void worker_loop(hk_server *sv, Worker *w) {
             std::memset(&o, 0, sizeof(o));
             o.eapca_th = -1.0f;
             o.sax_th = -1.0f;
+            o.flags = sv->opts.query_flags;
+            if (has_copt) o = copt;   // the collection's own configuration
             // graph mode records a pass per index into that index's one graph
             // work space, which concurrent batches would share: not served
-            o.flags = sv->opts.query_flags & ~(uint32_t)(HK_Q_TIMING | HK_Q_GRAPH);
+            o.flags &= ~(uint32_t)(HK_Q_TIMING | HK_Q_GRAPH);
             // the precision form where the collection has it (16-bit copy, n <= 256)
             if ((o.flags & HK_Q_BF16) && (!idx->has_bf16 || idx->n > hk::kTcMaxLen))
                 o.flags &= ~(uint32_t)HK_Q_BF16;
@@ -285,12 +293,34 @@ int hk_server_create(const hk_server_opts *opts, hk_server **out) {
 }
 
 int hk_server_add(hk_server *sv, hk_index *idx, int32_t *coll_id) {
+    return hk_server_add_opts(sv, idx, nullptr, coll_id);
+}
+
+int hk_server_add_opts(hk_server *sv, hk_index *idx, const hk_query_opts *opts, int32_t *coll_id) {
     try {
         hk::clear_last_error();
         if (!sv || !idx || !coll_id) hk::fail(HK_EINVAL, "NULL argument");
+        if (opts) {
+            // the checks hk_query applies to its options
+            const hk_query_opts &o = *opts;
+            if (o.l_max < 0) hk::fail(HK_EINVAL, "l_max=%d must be >= 0", o.l_max);
+            if (o.query_group < 0 || o.series_tile < 0) hk::fail(HK_EINVAL, "tile sizes must be >= 0");
+            if (o.flags & HK_Q_BF16) {
+                if (!idx->has_bf16)
+                    hk::fail(HK_EINVAL, "HK_Q_BF16 needs an index built with HK_BUILD_BF16 or HK_BUILD_FP16");
+                if (idx->n > hk::kTcMaxLen)
+                    hk::fail(HK_EINVAL, "HK_Q_BF16 takes series of length <= %d (n=%d)", hk::kTcMaxLen, idx->n);
+                if (o.flags & HK_Q_NOPRUNE)
+                    hk::fail(HK_EINVAL, "HK_Q_BF16 and HK_Q_NOPRUNE exclude each other");
+            }
+            if ((o.flags & HK_Q_TREE) && (o.flags & HK_Q_NOPRUNE))
+                hk::fail(HK_EINVAL, "HK_Q_TREE and HK_Q_NOPRUNE exclude each other");
+        }
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->colls.push_back(idx);
         sv->queues.emplace_back();
+        sv->copts.push_back(opts ? *opts : hk_query_opts{});
+        sv->has_copts.push_back(opts ? 1 : 0);
         *coll_id = (int32_t)sv->colls.size() - 1;
         return HK_OK;
     } catch (const hk::Error &e) {

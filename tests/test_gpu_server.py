@@ -222,3 +222,40 @@ def test_persistent_scan_relaunches_after_idle(hb, oracle_lib, two_collections):
         ids, dist, _ = c["idx"][ci].query(c["Q"][ci][qi:qi + 1], k, flags=flags)
         np.testing.assert_array_equal(r[0], ids[0])
         np.testing.assert_array_equal(r[1], dist[0])
+
+
+def test_collection_opts_and_tuned_configuration(hb, two_collections):
+    """hk_server_add_opts: each collection's batches run with its own query
+    configuration -- here hk_tune's choice for the float16 collection and two
+    hand-set ones for the float32 collection -- and every answer equals
+    hk_query's for the same query with the same options; invalid options are
+    refused when the collection is added."""
+    c = two_collections
+    keys = ("l_max", "eapca_th", "sax_th", "flags", "query_group", "series_tile")
+    tuned = c["idx"][1].tune(c["Q"][1][:32], 10)
+    tuned = {k: tuned[k] for k in keys}
+    hand = [dict(query_group=2, series_tile=4096, eapca_th=1.01, flags=hb.HK_Q_NOSAX),
+            dict(flags=hb.HK_Q_TREE, l_max=2)]
+    sv = hb.Server(max_batch=32, max_wait_us=200, workers=2)
+    setups = [(1, tuned), (0, hand[0]), (0, hand[1])]
+    coll = [sv.add(c["idx"][i], opts=o) for i, o in setups]
+    reqs = [(s, qi, k) for s in range(3) for qi, k in zip(range(40), [1, 10, 3, 10] * 10)]
+    tickets = [sv.submit(coll[s], c["Q"][setups[s][0]][qi], k) for s, qi, k in reqs]
+    got = [sv.poll(t, k, timeout_us=30_000_000) for t, (_, _, k) in zip(tickets, reqs)]
+    st = sv.stats()
+    assert st["served"] == len(reqs) and st["errors"] == 0
+    sv.close()
+    for (s, qi, k), r in zip(reqs, got):
+        i, o = setups[s]
+        ids, dist, _ = c["idx"][i].query(c["Q"][i][qi:qi + 1], k, **o)
+        np.testing.assert_array_equal(r[0], ids[0])
+        np.testing.assert_array_equal(r[1], dist[0])
+    sv = hb.Server()
+    for i, o in [(0, dict(flags=hb.HK_Q_BF16)),                       # no 16-bit copy
+                 (1, dict(flags=hb.HK_Q_BF16 | hb.HK_Q_NOPRUNE)),
+                 (0, dict(flags=hb.HK_Q_TREE | hb.HK_Q_NOPRUNE)),
+                 (0, dict(query_group=-1)), (0, dict(l_max=-2))]:
+        with pytest.raises(hb.HerculesError) as e:
+            sv.add(c["idx"][i], opts=o)
+        assert e.value.code == hb.HK_EINVAL
+    sv.close()
