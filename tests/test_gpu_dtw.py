@@ -33,6 +33,7 @@ def _wl():
     (5000, 128, 80, 8, 5, 12, [0.05, 1.0]),
     (3000, 256, 60, 6, 20, 16, [0.3]),
     (6000, 16, 50, 10, 7, 3, [0.2, 1.0]),
+    (20000, 64, 5000, 8, 10, 8, [0.5, 1.0]),     # leaves of thousands: several screening windows
 ])
 def test_dtw_matches_bruteforce(hb, oracle_lib, N, n, tau, nq, k, band, sig):
     wl = _wl()
