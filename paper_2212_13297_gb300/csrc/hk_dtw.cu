@@ -286,20 +286,22 @@ __device__ __forceinline__ float dtw_band(const float *__restrict__ x, const flo
 constexpr int kDtwWindow = 1024;   // series a block screens before their DTWs
 
 // a5-a6: one (leaf, query) pair per block at a time (persistent grid).  The
-// block screens a window of the leaf's series (word bound, then LB_Keogh:
-// one series per thread), queues the survivors in shared memory, then its
+// block screens a window of the leaf's series (the word bound, one series
+// per thread, then LB_Keogh, one series per warp), queues the survivors in
+// shared memory, then its
 // threads take queued series one at a time for the DTW with early
 // abandoning, so a thread whose series ended early takes the next.
 template <int KW>
-__global__ void __launch_bounds__(kDtwThreads) k_dtw_scan(DtwScanArgs A) {
+__global__ void __launch_bounds__(kDtwThreads, 4) k_dtw_scan(DtwScanArgs A) {
     extern __shared__ float sh[];
     const int n = A.n, r = A.r;
     float *qs = sh, *Ls = sh + n, *Us = sh + 2 * n;
     __shared__ float B[kAlpha + 1];
     __shared__ float pl[kWord], pu[kWord];
     __shared__ int64_t s_e;
-    __shared__ int s_qn, s_take;
-    __shared__ int16_t s_queue[kDtwWindow];
+    __shared__ int s_pn, s_qn, s_take;
+    __shared__ int16_t s_pre[kDtwWindow];     // the window's series left by the word bound
+    __shared__ int16_t s_queue[kDtwWindow];   // ... and by LB_Keogh: their DTWs to do
     for (int j = threadIdx.x; j <= kAlpha; j += blockDim.x)
         B[j] = j == 0 ? -INFINITY : (j == kAlpha ? INFINITY : A.bp[j - 1]);
     const float w_sax = (float)(n / kWord);
@@ -330,10 +332,12 @@ __global__ void __launch_bounds__(kDtwThreads) k_dtw_scan(DtwScanArgs A) {
         for (int64_t w0 = s0; w0 < s1; w0 += kDtwWindow) {
             const int64_t w1 = min(w0 + (int64_t)kDtwWindow, s1);
             if (threadIdx.x == 0) {
+                s_pn = 0;
                 s_qn = 0;
                 s_take = 0;
             }
             __syncthreads();
+            // the word bound, one series per thread
             for (int64_t s = w0 + threadIdx.x; s < w1; s += blockDim.x) {
                 ++c_cand;
                 if (A.use_sax) {
@@ -353,24 +357,40 @@ __global__ void __launch_bounds__(kDtwThreads) k_dtw_scan(DtwScanArgs A) {
                         continue;
                     }
                 }
-                const float *x = A.X + s * n;
-                // LB_Keogh from the raw points, rounded down, stopping once above U
-                float lbk = 0.0f;
-                bool pruned = false;
-                for (int j0 = 0; j0 < n && !pruned; j0 += 16) {
-#pragma unroll
-                    for (int j = j0; j < j0 + 16; ++j) {
-                        const float xv = x[j];
-                        const float g = fmaxf(fmaxf(__fsub_rd(Ls[j], xv), __fsub_rd(xv, Us[j])), 0.0f);
-                        lbk = __fmaf_rd(g, g, lbk);
+                s_pre[atomicAdd(&s_pn, 1)] = (int16_t)(s - w0);
+            }
+            __syncthreads();
+            // LB_Keogh from the raw points, one series per warp (lane l takes
+            // points 4l.., 4l+128.., so a row is read in coalesced 512-byte
+            // pieces); every partial sum rounded down, so the total stays
+            // below the exact bound
+            {
+                const int pn = s_pn, lane = threadIdx.x & 31;
+                const float4 *L4 = reinterpret_cast<const float4 *>(Ls);
+                const float4 *U4 = reinterpret_cast<const float4 *>(Us);
+                for (int i = threadIdx.x >> 5; i < pn; i += kDtwThreads / 32) {
+                    const int off = s_pre[i];
+                    const float4 *x4 = reinterpret_cast<const float4 *>(A.X + (w0 + off) * n);
+                    float part = 0.0f;
+                    for (int f = lane; f < (n >> 2); f += 32) {
+                        const float4 xv = x4[f], lv = L4[f], uv = U4[f];
+                        float g;
+                        g = fmaxf(fmaxf(__fsub_rd(lv.x, xv.x), __fsub_rd(xv.x, uv.x)), 0.0f);
+                        part = __fmaf_rd(g, g, part);
+                        g = fmaxf(fmaxf(__fsub_rd(lv.y, xv.y), __fsub_rd(xv.y, uv.y)), 0.0f);
+                        part = __fmaf_rd(g, g, part);
+                        g = fmaxf(fmaxf(__fsub_rd(lv.z, xv.z), __fsub_rd(xv.z, uv.z)), 0.0f);
+                        part = __fmaf_rd(g, g, part);
+                        g = fmaxf(fmaxf(__fsub_rd(lv.w, xv.w), __fsub_rd(xv.w, uv.w)), 0.0f);
+                        part = __fmaf_rd(g, g, part);
                     }
-                    pruned = lbk > u;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part = __fadd_rd(part, __shfl_xor_sync(0xffffffffu, part, o));
+                    if (lane == 0) {
+                        if (part > u) ++c_keogh;
+                        else s_queue[atomicAdd(&s_qn, 1)] = (int16_t)off;
+                    }
                 }
-                if (pruned) {
-                    ++c_keogh;
-                    continue;
-                }
-                s_queue[atomicAdd(&s_qn, 1)] = (int16_t)(s - w0);
             }
             __syncthreads();
             const int qn = s_qn;
