@@ -220,7 +220,7 @@ def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    rows = min(250_000, wl["N"])   # rows scanned per step (the collection's first rows)
+    rows = min(4_000_000, wl["N"])   # rows scanned per step (the collection's first rows)
     X = workload.random_walk(rows, wl["n"], seed=0, device="cpu").numpy()
     cores = len(os.sched_getaffinity(0))
     nqb = max(1, min(16, cores))
