@@ -420,13 +420,13 @@ def serve_mix(args):
 def ablation(args):
     """The paper's ablation (Sec. 4.2): the float32 path with and without
     LB_SAX filtering (NoSAX) and the EAPCA_TH / SAX_TH switches (NoThresh),
-    on the mid workload (10M x 256, 100 queries of mixed difficulty, k = 10).
-    Prints one JSON line."""
+    on the mid workload (10M x 256, 100 queries of mixed difficulty, k = 10)
+    or the one --ablation-workload names.  Prints one JSON line."""
     import torch
     from paper_2212_13297_gb300 import binding, workload
     import __graft_entry__
     __graft_entry__.build()
-    wl = WORKLOADS["mid"]
+    wl = WORKLOADS[args.ablation_workload]
     X = workload.random_walk(wl["N"], wl["n"], seed=0, device="cuda")
     Q, _ = workload.queries(X, wl["nq"], wl["sigmas"], seed=1)
     idx = binding.Index(X, wl["tau"])
@@ -602,7 +602,13 @@ def dtw_bench(args):
                          series_candidate_per_query=agg["series_candidate"] / agg["queries"],
                          word_bound_pruned_frac=agg["series_sax_pruned"] / max(1, agg["series_candidate"]),
                          keogh_or_abandoned_frac=agg["series_abandoned"] / max(1, agg["series_candidate"]),
-                         full_per_query=agg["series_full"] / agg["queries"])
+                         full_per_query=agg["series_full"] / agg["queries"],
+                         points_per_query=agg["points_computed"] / agg["queries"],
+                         points_per_s=agg["points_computed"] / t)
+    # DTW cells: a difference, a square and an addition each (3 flops), against
+    # the derived FP32 ALU peak the float32 scan reports against
+    alu_peak = 152 * 128 * 2 * 2070e6
+    out["dtw"]["alu_frac"] = 3 * out["dtw"]["points_per_s"] / alu_peak
     print(json.dumps(dict(metric="row f4: exact 10-NN under DTW (band %d) through the index" % band,
                           unit="queries/s", data="synthetic",
                           config=dict(workload="1M random walks x 256, leaf 1K, 100 queries (sigma 0.1/0.5), "
@@ -640,6 +646,7 @@ def main():
                     help="instrumented steps (kernel times by CUDA events) after the timed steps")
     ap.add_argument("--ablation", action="store_true",
                     help="instead of the step benchmark, the NoSAX / NoThresh ablation on the mid workload")
+    ap.add_argument("--ablation-workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--tune-graph", action="store_true",
                     help="instead of the step benchmark, hk_tune's choice against the defaults and "
                          "CUDA-graph replay against ordinary calls (10M x 256)")

@@ -206,80 +206,102 @@ struct DtwScanArgs {
     long long *st;
 };
 
-// Float32 DTW of series x against the query in shared memory, rows kept in
-// registers (cell w of row i is column j = i + w - r; cells past 2r stay
-// +inf), abandoned as soon as a row's smallest cell exceeds T: returns the
-// distance, and sets `abandoned` if it stopped early.  Rows whose band lies inside [0, n) take
-// a path without the column checks; the arithmetic per cell is the same.
-template <int KW>
-__device__ __forceinline__ float dtw_band(const float *__restrict__ x, const float *__restrict__ qs, int n,
-                                          int r, float T, long long &cells, bool &abandoned) {
-    float prev[KW + 1], cur[KW], xw[KW + 1];
-    const int wmax = 2 * r;
+// One row i of the banded DTW: cell w is column j = i + w - r, from the
+// row above (prev, +inf past the band) and the cell to its left; returns
+// the row's smallest cell.  Rows whose band lies inside [0, n) skip the
+// column checks; the arithmetic per cell is the same.
+template <int KW, bool kExact>
+__device__ __forceinline__ float dtw_row(int i, float qi, const float (&prev)[KW + 1], float (&cur)[KW + 1],
+                                         const float (&xw)[KW + 1], int n, int r) {
+    const int wmax = kExact ? KW - 1 : 2 * r;
+    float rowmin = INFINITY;
+    if (i >= r && i + r < n && i > 0) {
 #pragma unroll
-    for (int w = 0; w < KW; ++w) {
-        prev[w] = INFINITY;
-        cur[w] = INFINITY;
+        for (int w = 0; w < KW; ++w) {
+            if (w <= wmax) {
+                const float c = w >= 1 ? cur[w - 1] : INFINITY;
+                const float best = fminf(fminf(prev[w], prev[w + 1]), c);
+                const float d = __fsub_rn(qi, xw[w]);
+                const float v = __fadd_rn(__fmul_rn(d, d), best);
+                cur[w] = v;
+                rowmin = fminf(rowmin, v);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < KW; ++w) {
+            if (w <= wmax) {
+                const int j = i + w - r;
+                float v = INFINITY;
+                if (j >= 0 && j < n) {
+                    float best;
+                    if (i == 0 && j == 0) {
+                        best = 0.0f;
+                    } else {
+                        const float c = w >= 1 ? cur[w - 1] : INFINITY;
+                        best = fminf(fminf(prev[w], prev[w + 1]), c);
+                    }
+                    const float d = __fsub_rn(qi, xw[w]);
+                    v = __fadd_rn(__fmul_rn(d, d), best);
+                }
+                cur[w] = v;
+                rowmin = fminf(rowmin, v);
+            }
+        }
+    }
+    return rowmin;
+}
+
+// Slide the band's window of x one column right (the column entering at
+// row i + 1 is i + 1 + r).
+template <int KW, bool kExact>
+__device__ __forceinline__ void dtw_slide(float (&xw)[KW + 1], const float *__restrict__ x, int i, int n, int r) {
+    const int wmax = kExact ? KW - 1 : 2 * r;
+    const int jn = i + 1 + r;
+    const float xn = jn < n ? x[jn] : 0.0f;
+#pragma unroll
+    for (int w = 0; w < KW; ++w) xw[w] = (w == wmax) ? xn : xw[w + 1];
+}
+
+// Float32 DTW of series x against the query in shared memory, two rows in
+// registers used in turn (n is a multiple of 16, so rows come in pairs;
+// cells past the band stay +inf), abandoned as soon as a row's smallest
+// cell exceeds T: returns the distance, and sets `abandoned` if it stopped
+// early.  kExact: the band fills all KW cells (r = (KW - 1) / 2), so the
+// cell loop needs no test of the band's width.
+template <int KW, bool kExact>
+__device__ __forceinline__ float dtw_band(const float *__restrict__ x, const float *__restrict__ qs, int n,
+                                          int r_arg, float T, long long &cells, bool &abandoned) {
+    const int r = kExact ? (KW - 1) / 2 : r_arg;
+    const int wmax = kExact ? KW - 1 : 2 * r;
+    float pa[KW + 1], pb[KW + 1], xw[KW + 1];
+#pragma unroll
+    for (int w = 0; w <= KW; ++w) {
+        pa[w] = INFINITY;
+        pb[w] = INFINITY;
         const int j = w - r;                     // the window of row 0
         xw[w] = (w <= wmax && j >= 0 && j < n) ? x[j] : 0.0f;
     }
-    prev[KW] = INFINITY;
-    xw[KW] = 0.0f;
-    for (int i = 0; i < n; ++i) {
-        const float qi = qs[i];
-        float rowmin = INFINITY;
-        if (i >= r && i + r < n && i > 0) {
-            // every cell of the row inside the matrix
-#pragma unroll
-            for (int w = 0; w < KW; ++w) {
-                if (w <= wmax) {
-                    const float c = w >= 1 ? cur[w - 1] : INFINITY;
-                    const float best = fminf(fminf(prev[w], prev[w + 1]), c);
-                    const float d = __fsub_rn(qi, xw[w]);
-                    const float v = __fadd_rn(__fmul_rn(d, d), best);
-                    cur[w] = v;
-                    rowmin = fminf(rowmin, v);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int w = 0; w < KW; ++w) {
-                if (w <= wmax) {
-                    const int j = i + w - r;
-                    float v = INFINITY;
-                    if (j >= 0 && j < n) {
-                        float best;
-                        if (i == 0 && j == 0) {
-                            best = 0.0f;
-                        } else {
-                            const float c = w >= 1 ? cur[w - 1] : INFINITY;
-                            best = fminf(fminf(prev[w], prev[w + 1]), c);
-                        }
-                        const float d = __fsub_rn(qi, xw[w]);
-                        v = __fadd_rn(__fmul_rn(d, d), best);
-                    }
-                    cur[w] = v;
-                    rowmin = fminf(rowmin, v);
-                }
-            }
-        }
-        cells += wmax + 1;
-        if (rowmin > T) {
+    for (int i = 0; i < n; i += 2) {
+        float m = dtw_row<KW, kExact>(i, qs[i], pa, pb, xw, n, r);
+        dtw_slide<KW, kExact>(xw, x, i, n, r);
+        if (m > T) {
+            cells += wmax + 1;
             abandoned = true;
             return INFINITY;
         }
-        const int jn = i + 1 + r;              // the column entering the band
-        const float xn = jn < n ? x[jn] : 0.0f;
-#pragma unroll
-        for (int w = 0; w < KW; ++w) {
-            prev[w] = cur[w];
-            xw[w] = (w == wmax) ? xn : xw[w + 1];
+        m = dtw_row<KW, kExact>(i + 1, qs[i + 1], pb, pa, xw, n, r);
+        cells += 2 * (wmax + 1);
+        if (m > T) {
+            abandoned = true;
+            return INFINITY;
         }
+        dtw_slide<KW, kExact>(xw, x, i + 1, n, r);
     }
-    float d = INFINITY;                        // column n - 1 of row n - 1: cell r
+    float d = INFINITY;                        // column n - 1 of row n - 1 (odd): cell r of pa
 #pragma unroll
     for (int w = 0; w < KW; ++w)
-        if (w == r) d = prev[w];
+        if (w == r) d = pa[w];
     return d;
 }
 
@@ -399,7 +421,8 @@ __global__ void __launch_bounds__(kDtwThreads, 4) k_dtw_scan(DtwScanArgs A) {
                 if (idx >= qn) break;
                 const int64_t s = w0 + s_queue[idx];
                 bool abandoned = false;
-                const float d = dtw_band<KW>(A.X + s * n, qs, n, r, T, c_cells, abandoned);
+                const float d = 2 * r + 1 == KW ? dtw_band<KW, true>(A.X + s * n, qs, n, r, T, c_cells, abandoned)
+                                                : dtw_band<KW, false>(A.X + s * n, qs, n, r, T, c_cells, abandoned);
                 if (abandoned) {
                     ++c_ab;
                     continue;
