@@ -27,8 +27,11 @@
 // its word's bound and then by LB_Keogh, the rest get the float32 DTW with
 // early abandoning (every path crosses every row, so a row whose smallest cell
 // exceeds T(U) ends the series).  A float32 DTW is within rho = gamma_{2n+4}
-// of D (a path has at most 2n - 1 cells, each cost three roundings, each sum
-// one); series with float32 distance <= T(U) = U(1 + rho) go to the query's
+// of D: a cell rounds its difference, then adds its square to the best
+// neighbour in one fused multiply-add (one rounding), so a path of at most
+// 2n - 1 cells is a recursive sum of its costs, each carrying (1 + delta)^2,
+// within gamma_{2n+1} of its exact value, and the minimum over paths is
+// exact; series with float32 distance <= T(U) = U(1 + rho) go to the query's
 // pool, and the final step rescores the pool's entries <= T(U_final) in
 // binary64.  A pool that overflows makes its query run again from its pool's
 // (tighter) bound.
@@ -208,9 +211,9 @@ struct DtwScanArgs {
 
 // One row i of the banded DTW: cell w is column j = i + w - r, from the
 // row above (prev, +inf past the band) and the cell to its left; returns
-// the row's smallest cell.  Rows whose band lies inside [0, n) skip the
+// the row's smallest cell (kMin; +inf otherwise).  Rows whose band lies inside [0, n) skip the
 // column checks; the arithmetic per cell is the same.
-template <int KW, bool kExact>
+template <int KW, bool kExact, bool kMin>
 __device__ __forceinline__ float dtw_row(int i, float qi, const float (&prev)[KW + 1], float (&cur)[KW + 1],
                                          const float (&xw)[KW + 1], int n, int r) {
     const int wmax = kExact ? KW - 1 : 2 * r;
@@ -222,9 +225,9 @@ __device__ __forceinline__ float dtw_row(int i, float qi, const float (&prev)[KW
                 const float c = w >= 1 ? cur[w - 1] : INFINITY;
                 const float best = fminf(fminf(prev[w], prev[w + 1]), c);
                 const float d = __fsub_rn(qi, xw[w]);
-                const float v = __fadd_rn(__fmul_rn(d, d), best);
+                const float v = __fmaf_rn(d, d, best);
                 cur[w] = v;
-                rowmin = fminf(rowmin, v);
+                if (kMin) rowmin = fminf(rowmin, v);
             }
         }
     } else {
@@ -242,10 +245,10 @@ __device__ __forceinline__ float dtw_row(int i, float qi, const float (&prev)[KW
                         best = fminf(fminf(prev[w], prev[w + 1]), c);
                     }
                     const float d = __fsub_rn(qi, xw[w]);
-                    v = __fadd_rn(__fmul_rn(d, d), best);
+                    v = __fmaf_rn(d, d, best);
                 }
                 cur[w] = v;
-                rowmin = fminf(rowmin, v);
+                if (kMin) rowmin = fminf(rowmin, v);
             }
         }
     }
@@ -265,9 +268,9 @@ __device__ __forceinline__ void dtw_slide(float (&xw)[KW + 1], const float *__re
 
 // Float32 DTW of series x against the query in shared memory, two rows in
 // registers used in turn (n is a multiple of 16, so rows come in pairs;
-// cells past the band stay +inf), abandoned as soon as a row's smallest
-// cell exceeds T: returns the distance, and sets `abandoned` if it stopped
-// early.  kExact: the band fills all KW cells (r = (KW - 1) / 2), so the
+// cells past the band stay +inf), abandoned once the smallest cell of the
+// second row of a pair exceeds T (every path crosses that row, so D > T):
+// returns the distance, and sets `abandoned` if it stopped early.  kExact: the band fills all KW cells (r = (KW - 1) / 2), so the
 // cell loop needs no test of the band's width.
 template <int KW, bool kExact>
 __device__ __forceinline__ float dtw_band(const float *__restrict__ x, const float *__restrict__ qs, int n,
@@ -283,14 +286,9 @@ __device__ __forceinline__ float dtw_band(const float *__restrict__ x, const flo
         xw[w] = (w <= wmax && j >= 0 && j < n) ? x[j] : 0.0f;
     }
     for (int i = 0; i < n; i += 2) {
-        float m = dtw_row<KW, kExact>(i, qs[i], pa, pb, xw, n, r);
+        dtw_row<KW, kExact, false>(i, qs[i], pa, pb, xw, n, r);
         dtw_slide<KW, kExact>(xw, x, i, n, r);
-        if (m > T) {
-            cells += wmax + 1;
-            abandoned = true;
-            return INFINITY;
-        }
-        m = dtw_row<KW, kExact>(i + 1, qs[i + 1], pb, pa, xw, n, r);
+        const float m = dtw_row<KW, kExact, true>(i + 1, qs[i + 1], pb, pa, xw, n, r);
         cells += 2 * (wmax + 1);
         if (m > T) {
             abandoned = true;
