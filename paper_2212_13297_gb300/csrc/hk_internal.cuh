@@ -387,9 +387,11 @@ constexpr int kTcLocalK = 16;     // largest k whose best upper bounds the tenso
 // Candidate-list and pool length per query in the precision form: its
 // certified band admits the near neighbours around the k-th distance, more
 // of them as k grows (an overflow reruns the query on the float32 path).
+// At least 262,144: with a bfloat16 copy (band 8x float16's) hard queries
+// average about 9K candidates at 100M x 256, with a tail past 65K.
 inline int tc_list_cap(int k) {
     const int c = k * 4096 < (1 << 20) ? k * 4096 : (1 << 20);
-    return c > 65536 ? c : 65536;
+    return c > 262144 ? c : 262144;
 }
 
 // Exhaustive exact k-NN into caller device buffers using only `sc`.

@@ -97,26 +97,37 @@ struct hk_server {
 
 namespace {
 
+// Whether a collection's batches take the precision form.  Called with
+// sv->mu held.
+bool coll_tc(const hk_server *sv, int coll) {
+    const hk_index *idx = sv->colls[coll];
+    const uint32_t f = sv->has_copts[coll] ? sv->copts[coll].flags : sv->opts.query_flags;
+    return (f & HK_Q_BF16) && idx->has_bf16 && idx->n <= hk::kTcMaxLen;
+}
+
 // Device bytes of query work space per query of a batch on this index
-// (pessimistic: precision-form pools and candidate lists included).
-int64_t bytes_per_query(const hk_index *idx, int k) {
+// (pessimistic: the form's largest pools and candidate lists).
+int64_t bytes_per_query(const hk_index *idx, int k, bool tc) {
     const int64_t L = idx->L, n = idx->n;
-    const int64_t pool = hk::tc_list_cap(k);
+    const int64_t pool = tc ? hk::tc_list_cap(k) : 65536;
     return L * (1 + 4 + 8) + n * 4 * 2 + idx->S * 16 + 16 * 256 * 2 + pool * 16 +
            pool * 8 + 64 * (int64_t)k;
 }
 
 // Device bytes a batch of nq queries with this k holds while in flight
 // (its work space and its retry work space).
-int64_t batch_bytes(const hk_index *idx, int k, int nq) { return bytes_per_query(idx, k) * 2 * nq; }
+int64_t batch_bytes(const hk_index *idx, int k, int nq, bool tc) {
+    return bytes_per_query(idx, k, tc) * 2 * nq;
+}
 
 // Most requests a batch may take now: max_batch, and what the budget has
 // room for beside the batches in flight (at least one when none is).
 // Called with sv->mu held.
-int batch_cap(hk_server *sv, const hk_index *idx, int k) {
+int batch_cap(hk_server *sv, int coll, int k) {
+    const hk_index *idx = sv->colls[coll];
     int cap = sv->opts.max_batch > 0 ? sv->opts.max_batch : 1024;
     if (sv->opts.hbm_budget > 0) {
-        const int64_t per = std::max<int64_t>(1, batch_bytes(idx, k, 1));
+        const int64_t per = std::max<int64_t>(1, batch_bytes(idx, k, 1, coll_tc(sv, coll)));
         const int64_t room = sv->opts.hbm_budget - sv->budget_used;
         const int64_t fit = room > 0 ? room / per : 0;
         cap = (int)std::min<int64_t>(cap, fit);
@@ -169,14 +180,14 @@ void worker_loop(hk_server *sv, Worker *w) {
             if (sv->opts.max_wait_us > 0) {
                 const auto until = Clock::now() + std::chrono::microseconds(sv->opts.max_wait_us);
                 const int kmax_guess = sv->queues[coll].front()->k;
-                const int cap = batch_cap(sv, sv->colls[coll], kmax_guess);
+                const int cap = batch_cap(sv, coll, kmax_guess);
                 while ((int)sv->queues[coll].size() < cap && Clock::now() < until && !sv->stop)
                     sv->cv_work.wait_until(lk, until);
             }
             if (sv->queues[coll].empty()) continue;
             int kmax = 0;
             for (auto &r : sv->queues[coll]) kmax = std::max(kmax, r->k);
-            const int cap = batch_cap(sv, sv->colls[coll], kmax);
+            const int cap = batch_cap(sv, coll, kmax);
             if (cap < 1) {
                 // the budget is taken by batches in flight: wait for one to finish
                 sv->cv_mem.wait_for(lk, std::chrono::milliseconds(5));
@@ -189,7 +200,7 @@ void worker_loop(hk_server *sv, Worker *w) {
             has_copt = sv->has_copts[coll] != 0;
             if (has_copt) copt = sv->copts[coll];
             if (sv->opts.hbm_budget > 0) {
-                reserved = batch_bytes(sv->colls[coll], kmax, (int)batch.size());
+                reserved = batch_bytes(sv->colls[coll], kmax, (int)batch.size(), coll_tc(sv, coll));
                 sv->budget_used += reserved;
                 sv->budget_peak = std::max(sv->budget_peak, sv->budget_used);
             }
