@@ -200,3 +200,21 @@ def test_tc_bound_adversarial(hb, kind, n, fmt):
     lo64, up64 = lo.astype(np.float64), up.astype(np.float64)
     assert (lo64 <= exact).all(), (kind, float((lo64 - exact).max()))
     assert (up64 >= exact).all(), (kind, float((exact - up64).max()))
+
+
+def test_tc_candidate_list_overflow_reruns_exactly(hb, oracle_lib):
+    """A query whose certified band admits more candidates than its list
+    holds (300,000 copies of one row: every copy is a candidate) is rerun on
+    the float32 path and still gets the exact answer, ties to the lower id."""
+    wl = _wl()
+    base = wl.random_walk(1, 16, seed=31, device="cuda")
+    other = wl.random_walk(2000, 16, seed=32, device="cuda")
+    X = torch.cat([other[:1000], base.repeat(300_000, 1), other[1000:]]).contiguous()
+    Q = torch.cat([base, wl.queries(other, 2, 0.5, seed=33)[0]]).contiguous()
+    idx = hb.Index(X, 10_000, flags=hb.HK_BUILD_FP16)
+    ids, dist, st = idx.query(Q, 3, flags=hb.HK_Q_BF16)
+    oids, od2 = oracle.knn(X.cpu().numpy(), Q.cpu().numpy(), 3)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    np.testing.assert_allclose(dist.cpu().numpy(), np.sqrt(od2).astype(np.float32), rtol=1e-5)
+    assert list(ids[0].cpu().numpy()) == [1000, 1001, 1002]
+    assert st["retried_queries"] >= 1
