@@ -33,6 +33,18 @@ void tc_wait_hooks(uint64_t &wait_ns, int &stall) {
     wait_ns = g_tc_wait_ns.load();
     stall = g_tc_stall.load();
 }
+
+void check_query_opts(const hk_index *idx, const hk_query_opts &o) {
+    if (o.l_max < 0) fail(HK_EINVAL, "l_max=%d must be >= 0", o.l_max);
+    if (o.query_group < 0 || o.series_tile < 0) fail(HK_EINVAL, "tile sizes must be >= 0");
+    if (o.flags & HK_Q_BF16) {
+        if (!idx->has_bf16) fail(HK_EINVAL, "HK_Q_BF16 needs an index built with HK_BUILD_BF16 or HK_BUILD_FP16");
+        if (idx->n > kTcMaxLen) fail(HK_EINVAL, "HK_Q_BF16 takes series of length <= %d (n=%d)", kTcMaxLen, idx->n);
+        if (o.flags & HK_Q_NOPRUNE) fail(HK_EINVAL, "HK_Q_BF16 and HK_Q_NOPRUNE exclude each other");
+    }
+    if ((o.flags & HK_Q_TREE) && (o.flags & HK_Q_NOPRUNE))
+        fail(HK_EINVAL, "HK_Q_TREE and HK_Q_NOPRUNE exclude each other");
+}
 }  // namespace hk
 
 namespace {
@@ -189,17 +201,7 @@ int hk_query(hk_index *idx, const float *Q, int32_t nq, int32_t k, const hk_quer
             o.eapca_th = -1.0f;
             o.sax_th = -1.0f;
         }
-        if (o.l_max < 0) hk::fail(HK_EINVAL, "l_max=%d must be >= 0", o.l_max);
-        if (o.query_group < 0 || o.series_tile < 0) hk::fail(HK_EINVAL, "tile sizes must be >= 0");
-        if (o.flags & HK_Q_BF16) {
-            if (!idx->has_bf16)
-                hk::fail(HK_EINVAL, "HK_Q_BF16 needs an index built with HK_BUILD_BF16 or HK_BUILD_FP16");
-            if (idx->n > hk::kTcMaxLen)
-                hk::fail(HK_EINVAL, "HK_Q_BF16 takes series of length <= %d (n=%d)", hk::kTcMaxLen, idx->n);
-            if (o.flags & HK_Q_NOPRUNE) hk::fail(HK_EINVAL, "HK_Q_BF16 and HK_Q_NOPRUNE exclude each other");
-        }
-        if ((o.flags & HK_Q_TREE) && (o.flags & HK_Q_NOPRUNE))
-            hk::fail(HK_EINVAL, "HK_Q_TREE and HK_Q_NOPRUNE exclude each other");
+        hk::check_query_opts(idx, o);
         cudaStream_t s = (cudaStream_t)stream;
         idx->stream = s;
         // host queries go through the index's staging buffer: no device

@@ -254,6 +254,8 @@ void build_index(hk_index *idx, const float *X, int64_t N, int n, const hk_build
 // Device copies of the tree arrays (from the h_tree_* / h_inode_* vectors);
 // sizes ienv (filled by the caller).  Also forms the level lists.
 void upload_tree(hk_index *idx, cudaStream_t s);
+// The checks hk_query applies to its options on this index (HK_EINVAL).
+void check_query_opts(const hk_index *idx, const hk_query_opts &o);
 // Query (hk_query.cu)
 void run_query(hk_index *idx, const float *Qdev, int nq, int k, const hk_query_opts &o,
                cudaStream_t s, int64_t *out_ids_host_or_dev, float *out_dist_host_or_dev,

@@ -311,22 +311,7 @@ int hk_server_add_opts(hk_server *sv, hk_index *idx, const hk_query_opts *opts, 
     try {
         hk::clear_last_error();
         if (!sv || !idx || !coll_id) hk::fail(HK_EINVAL, "NULL argument");
-        if (opts) {
-            // the checks hk_query applies to its options
-            const hk_query_opts &o = *opts;
-            if (o.l_max < 0) hk::fail(HK_EINVAL, "l_max=%d must be >= 0", o.l_max);
-            if (o.query_group < 0 || o.series_tile < 0) hk::fail(HK_EINVAL, "tile sizes must be >= 0");
-            if (o.flags & HK_Q_BF16) {
-                if (!idx->has_bf16)
-                    hk::fail(HK_EINVAL, "HK_Q_BF16 needs an index built with HK_BUILD_BF16 or HK_BUILD_FP16");
-                if (idx->n > hk::kTcMaxLen)
-                    hk::fail(HK_EINVAL, "HK_Q_BF16 takes series of length <= %d (n=%d)", hk::kTcMaxLen, idx->n);
-                if (o.flags & HK_Q_NOPRUNE)
-                    hk::fail(HK_EINVAL, "HK_Q_BF16 and HK_Q_NOPRUNE exclude each other");
-            }
-            if ((o.flags & HK_Q_TREE) && (o.flags & HK_Q_NOPRUNE))
-                hk::fail(HK_EINVAL, "HK_Q_TREE and HK_Q_NOPRUNE exclude each other");
-        }
+        if (opts) hk::check_query_opts(idx, *opts);
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->colls.push_back(idx);
         sv->queues.emplace_back();
