@@ -211,8 +211,9 @@ struct DtwScanArgs {
 
 // One row i of the banded DTW: cell w is column j = i + w - r, from the
 // row above (prev, +inf past the band) and the cell to its left; returns
-// the row's smallest cell (kMin; +inf otherwise).  Rows whose band lies inside [0, n) skip the
-// column checks; the arithmetic per cell is the same.
+// the row's smallest cell (with kMin; +inf otherwise).  Rows whose band
+// lies inside [0, n) skip the column checks; the arithmetic per cell is the
+// same.
 template <int KW, bool kExact, bool kMin>
 __device__ __forceinline__ float dtw_row(int i, float qi, const float (&prev)[KW + 1], float (&cur)[KW + 1],
                                          const float (&xw)[KW + 1], int n, int r) {
@@ -270,8 +271,9 @@ __device__ __forceinline__ void dtw_slide(float (&xw)[KW + 1], const float *__re
 // registers used in turn (n is a multiple of 16, so rows come in pairs;
 // cells past the band stay +inf), abandoned once the smallest cell of the
 // second row of a pair exceeds T (every path crosses that row, so D > T):
-// returns the distance, and sets `abandoned` if it stopped early.  kExact: the band fills all KW cells (r = (KW - 1) / 2), so the
-// cell loop needs no test of the band's width.
+// returns the distance, and sets `abandoned` if it stopped early.
+// kExact: the band fills all KW cells (r = (KW - 1) / 2), so the cell loop
+// needs no test of the band's width.
 template <int KW, bool kExact>
 __device__ __forceinline__ float dtw_band(const float *__restrict__ x, const float *__restrict__ qs, int n,
                                           int r_arg, float T, long long &cells, bool &abandoned) {
@@ -308,9 +310,9 @@ constexpr int kDtwWindow = 1024;   // series a block screens before their DTWs
 // a5-a6: one (leaf, query) pair per block at a time (persistent grid).  The
 // block screens a window of the leaf's series (the word bound, one series
 // per thread, then LB_Keogh, one series per warp), queues the survivors in
-// shared memory, then its
-// threads take queued series one at a time for the DTW with early
-// abandoning, so a thread whose series ended early takes the next.
+// shared memory, then its threads take queued series one at a time for the
+// DTW with early abandoning, so a thread whose series ended early takes the
+// next.
 template <int KW>
 __global__ void __launch_bounds__(kDtwThreads, 4) k_dtw_scan(DtwScanArgs A) {
     extern __shared__ float sh[];
