@@ -643,7 +643,8 @@ def main():
                     help="the same for the float32 path, at a rate it sustains (0: off)")
     ap.add_argument("--serve-plain-seconds", type=float, default=2.5)
     ap.add_argument("--timing-steps", type=int, default=3,
-                    help="instrumented steps (kernel times by CUDA events) after the timed steps")
+                    help="instrumented steps (kernel times by CUDA events) after the timed steps; "
+                         "at least 1 (the roofline needs them)")
     ap.add_argument("--ablation", action="store_true",
                     help="instead of the step benchmark, the NoSAX / NoThresh ablation on the mid workload")
     ap.add_argument("--ablation-workload", default="mid", choices=sorted(WORKLOADS))
@@ -662,6 +663,7 @@ def main():
                     help="instead of the step benchmark, serve the four-collection mix at this "
                          "rate (requests/s) and print its latency line")
     args = ap.parse_args()
+    args.timing_steps = max(1, args.timing_steps)
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
         wl["batch"] = args.batch
