@@ -268,9 +268,9 @@ __device__ __forceinline__ void dtw_slide(float (&xw)[KW + 1], const float *__re
 }
 
 // Float32 DTW of series x against the query in shared memory, two rows in
-// registers used in turn (n is a multiple of 16, so rows come in pairs;
-// cells past the band stay +inf), abandoned once the smallest cell of the
-// second row of a pair exceeds T (every path crosses that row, so D > T):
+// registers used in turn (n is a multiple of 16, so rows come in groups of
+// four; cells past the band stay +inf), abandoned once the smallest cell of
+// the last row of a group exceeds T (every path crosses that row, so D > T):
 // returns the distance, and sets `abandoned` if it stopped early.
 // kExact: the band fills all KW cells (r = (KW - 1) / 2), so the cell loop
 // needs no test of the band's width.
@@ -287,18 +287,22 @@ __device__ __forceinline__ float dtw_band(const float *__restrict__ x, const flo
         const int j = w - r;                     // the window of row 0
         xw[w] = (w <= wmax && j >= 0 && j < n) ? x[j] : 0.0f;
     }
-    for (int i = 0; i < n; i += 2) {
+    for (int i = 0; i < n; i += 4) {
         dtw_row<KW, kExact, false>(i, qs[i], pa, pb, xw, n, r);
         dtw_slide<KW, kExact>(xw, x, i, n, r);
-        const float m = dtw_row<KW, kExact, true>(i + 1, qs[i + 1], pb, pa, xw, n, r);
-        cells += 2 * (wmax + 1);
+        dtw_row<KW, kExact, false>(i + 1, qs[i + 1], pb, pa, xw, n, r);
+        dtw_slide<KW, kExact>(xw, x, i + 1, n, r);
+        dtw_row<KW, kExact, false>(i + 2, qs[i + 2], pa, pb, xw, n, r);
+        dtw_slide<KW, kExact>(xw, x, i + 2, n, r);
+        const float m = dtw_row<KW, kExact, true>(i + 3, qs[i + 3], pb, pa, xw, n, r);
+        cells += 4 * (wmax + 1);
         if (m > T) {
             abandoned = true;
             return INFINITY;
         }
-        dtw_slide<KW, kExact>(xw, x, i + 1, n, r);
+        dtw_slide<KW, kExact>(xw, x, i + 3, n, r);
     }
-    float d = INFINITY;                        // column n - 1 of row n - 1 (odd): cell r of pa
+    float d = INFINITY;                        // column n - 1 of row n - 1 (n % 4 == 3): cell r of pa
 #pragma unroll
     for (int w = 0; w < KW; ++w)
         if (w == r) d = pa[w];
